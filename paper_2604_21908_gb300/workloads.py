@@ -1,0 +1,262 @@
+"""Seeded synthetic mirrored circuits (inputs only; none of the contraction method lives here).
+
+These generators stand in for the paper's HQAP benchmark circuits (Sec. III, a 56-qubit
+circuit with 1,917 two-qubit gates built as a mirrored U U^dagger block with swap
+obfuscation, Sec. I).  The circuit files themselves are not available, so every workload
+here is synthesised from a seed with the same structure:
+
+* a brickwork mirror on a line (the unobfuscated case the Middle-MPO attack solves, Sec. I);
+* an all-to-all mirror whose two halves are separated by a hidden qubit permutation
+  written as innocuous-looking two-qubit gates (the swap obfuscation unswapping removes,
+  Sec. II.B.2), with a per-gate perturbation exp(i eps H) on the mirrored half so the
+  output is peaked but not exactly a basis state.
+
+Both the oracle and the GPU library consume exactly the arrays produced here: logical
+qubit pairs ``pairs[g] = (a, b)`` (gate basis index ``2*x_a + x_b``), FP64 4x4 matrices,
+the split index between the right (earlier) and left (later) halves, and a final layer of
+one-qubit gates (the planted X^s).  Bit order for bitstrings: ``bits[q]`` is logical qubit
+q; a statevector index is ``sum_q bits[q] * 2**q``.
+
+Random numbers: numpy PCG64 seeded by ``SeedSequence(260421908, spawn_key=(family, seed))``.
+Haar SU(4) follows Mezzadri (2007): QR of a complex Ginibre matrix with the phases of
+R's diagonal moved into Q, then divided by det^(1/4).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ROOT_SEED = 260421908
+
+SWAP4 = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+X2 = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+
+
+@dataclass
+class Circuit:
+    """A gate list in time order plus the split point and the final one-qubit layer."""
+
+    n_qubits: int
+    pairs: np.ndarray                 # int32 [G, 2] logical qubits, pairs[g, 0] is the MSB of the gate basis
+    mats: np.ndarray                  # complex128 [G, 4, 4]
+    split_index: int                  # gates[:split] form the right (earlier) half C_R
+    oneq_qubits: np.ndarray           # int32 [K] one-qubit gates applied after every two-qubit gate
+    oneq_mats: np.ndarray             # complex128 [K, 2, 2]
+    planted: np.ndarray | None = None  # uint8 [n] the bitstring s the circuit is built to peak on
+    permutation: np.ndarray | None = None  # int32 [n] hidden permutation pi (qubit q -> pi[q])
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_gates(self) -> int:
+        return int(self.pairs.shape[0])
+
+    def mats_interleaved(self) -> np.ndarray:
+        """[G, 4, 4, 2] float64 (re, im), the layout the C library takes."""
+        return np.ascontiguousarray(np.stack([self.mats.real, self.mats.imag], axis=-1))
+
+    def oneq_interleaved(self) -> np.ndarray:
+        return np.ascontiguousarray(np.stack([self.oneq_mats.real, self.oneq_mats.imag], axis=-1))
+
+
+def rng_for(family: int, seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(ROOT_SEED, spawn_key=(family, seed))))
+
+
+def haar_unitary(rng: np.random.Generator, d: int = 4) -> np.ndarray:
+    z = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    ph = np.diag(r) / np.abs(np.diag(r))
+    return q * ph[None, :]
+
+
+def haar_su4(rng: np.random.Generator) -> np.ndarray:
+    u = haar_unitary(rng, 4)
+    det = np.linalg.det(u)
+    return u / det ** 0.25
+
+
+def polar_unitarize(g: np.ndarray) -> np.ndarray:
+    """Nearest unitary to g (polar factor), via the FP64 eigendecomposition of g^dagger g."""
+    w, v = np.linalg.eigh(g.conj().T @ g)
+    return g @ (v * (1.0 / np.sqrt(w))[None, :]) @ v.conj().T
+
+
+def through_complex64(g: np.ndarray) -> np.ndarray:
+    """A gate stored as complex64, read back as FP64 and re-unitarised."""
+    return polar_unitarize(g.astype(np.complex64).astype(np.complex128))
+
+
+def random_traceless_hermitian(rng: np.random.Generator, d: int = 4) -> np.ndarray:
+    z = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    h = 0.5 * (z + z.conj().T)
+    h = h - np.trace(h) / d * np.eye(d)
+    return h / np.max(np.abs(np.linalg.eigvalsh(h)))
+
+
+def expi_hermitian(h: np.ndarray, eps: float) -> np.ndarray:
+    w, v = np.linalg.eigh(h)
+    return (v * np.exp(1j * eps * w)[None, :]) @ v.conj().T
+
+
+def relabel_gate(pair, perm):
+    return (int(perm[pair[0]]), int(perm[pair[1]]))
+
+
+def permutation_transpositions(perm: np.ndarray) -> list[tuple[int, int]]:
+    """SWAPs (time order) that move the state of qubit q to qubit perm[q].
+
+    A cycle c0 -> c1 -> ... -> c_{L-1} -> c0 is realised by SWAP(c0,c1), SWAP(c0,c2), ...,
+    SWAP(c0,c_{L-1}).
+    """
+    n = len(perm)
+    seen = np.zeros(n, dtype=bool)
+    out = []
+    for start in range(n):
+        if seen[start]:
+            continue
+        cyc = [start]
+        seen[start] = True
+        q = int(perm[start])
+        while q != start:
+            cyc.append(q)
+            seen[q] = True
+            q = int(perm[q])
+        for k in range(1, len(cyc)):
+            out.append((cyc[0], cyc[k]))
+    return out
+
+
+def _oneq_layer(planted: np.ndarray):
+    qs = np.nonzero(planted)[0].astype(np.int32)
+    mats = np.repeat(X2[None], len(qs), axis=0)
+    return qs, mats
+
+
+def brickwork_mirror(n: int, layers: int, seed: int = 0) -> Circuit:
+    """X^s . U^dagger . U with U a brickwork of Haar SU(4) gates on a line (no permutation).
+
+    U has `layers` layers, alternating even bonds (0,1),(2,3),... and odd bonds.  The
+    right half C_R is U; the left half is U^dagger followed by X^s.
+    """
+    rng = rng_for(1, seed)
+    pairs, mats = [], []
+    for layer in range(layers):
+        for a in range(layer % 2, n - 1, 2):
+            pairs.append((a, a + 1))
+            mats.append(haar_su4(rng))
+    g_half = len(pairs)
+    for k in range(g_half - 1, -1, -1):
+        pairs.append(pairs[k])
+        mats.append(mats[k].conj().T)
+    planted = rng.integers(0, 2, size=n).astype(np.uint8)
+    oq, om = _oneq_layer(planted)
+    return Circuit(n, np.array(pairs, dtype=np.int32), np.array(mats), g_half, oq, om, planted,
+                   np.arange(n, dtype=np.int32), {"family": "brickwork_mirror", "layers": layers, "seed": seed})
+
+
+def hidden_permutation_mirror(n: int, gates_per_half: int, eps_pert: float, seed: int = 0,
+                              store_complex64: bool = True, family: int = 2) -> Circuit:
+    """X^s . V^dagger . P_pi . U with V = P_pi U P_pi^dagger, so C|0> = |s> when eps_pert = 0.
+
+    * U: `gates_per_half` Haar SU(4) gates on uniformly random distinct pairs (a, b).
+    * P_pi: a seeded random permutation written as transpositions; each transposition
+      (a, b) becomes the two gates R then SWAP.R^dagger on (a, b) with R Haar, so no SWAP
+      appears in the gate list.
+    * V^dagger: U's gates relabelled by pi, in reverse time order, adjoint, each
+      left-multiplied by exp(i eps_pert H_k) with H_k a random traceless Hermitian of unit
+      spectral norm.
+    * X^s: a final layer of X gates on the planted bitstring s.
+    With store_complex64 the U gates go through complex64 and are re-unitarised in FP64
+    before the mirror is built, so the mirror stays exact in FP64.
+    """
+    rng = rng_for(family, seed)
+    cast = through_complex64 if store_complex64 else (lambda g: g)
+    u_pairs, u_mats = [], []
+    for _ in range(gates_per_half):
+        a, b = rng.choice(n, size=2, replace=False)
+        u_pairs.append((int(a), int(b)))
+        u_mats.append(cast(haar_su4(rng)))
+    perm = rng.permutation(n).astype(np.int32)
+    p_pairs, p_mats = [], []
+    for (a, b) in permutation_transpositions(perm):
+        r = cast(haar_su4(rng))
+        p_pairs += [(a, b), (a, b)]
+        p_mats += [r, SWAP4 @ r.conj().T]
+    v_pairs, v_mats = [], []
+    for k in range(gates_per_half - 1, -1, -1):
+        g = u_mats[k].conj().T
+        if eps_pert != 0.0:
+            g = expi_hermitian(random_traceless_hermitian(rng), eps_pert) @ g
+        v_pairs.append(relabel_gate(u_pairs[k], perm))
+        v_mats.append(g)
+    planted = rng.integers(0, 2, size=n).astype(np.uint8)
+    oq, om = _oneq_layer(planted)
+    pairs = np.array(u_pairs + p_pairs + v_pairs, dtype=np.int32)
+    mats = np.array(u_mats + p_mats + v_mats)
+    split = len(pairs) // 2
+    return Circuit(n, pairs, mats, split, oq, om, planted, perm,
+                   {"family": "hidden_permutation_mirror", "gates_per_half": gates_per_half,
+                    "eps_pert": eps_pert, "seed": seed, "n_perm_gates": len(p_pairs)})
+
+
+def random_circuit(n: int, n_gates: int, seed: int = 0, line: bool = False) -> Circuit:
+    """A circuit with no mirror structure (Haar gates on random pairs), for checks where
+    the MPO must reproduce an arbitrary unitary."""
+    rng = rng_for(3, seed)
+    pairs, mats = [], []
+    for _ in range(n_gates):
+        if line:
+            a = int(rng.integers(0, n - 1))
+            pr = (a, a + 1) if rng.integers(0, 2) == 0 else (a + 1, a)
+        else:
+            a, b = rng.choice(n, size=2, replace=False)
+            pr = (int(a), int(b))
+        pairs.append(pr)
+        mats.append(haar_su4(rng))
+    return Circuit(n, np.array(pairs, dtype=np.int32).reshape(-1, 2), np.array(mats).reshape(-1, 4, 4),
+                   n_gates // 2, np.zeros(0, np.int32), np.zeros((0, 2, 2), np.complex128), None, None,
+                   {"family": "random", "seed": seed})
+
+
+def permutation_only(n: int, seed: int = 0, planted: bool = True) -> Circuit:
+    """C = X^s . P_pi with P_pi written as a SWAP network over the transpositions of pi."""
+    rng = rng_for(4, seed)
+    perm = rng.permutation(n).astype(np.int32)
+    pairs = permutation_transpositions(perm)
+    mats = [SWAP4.copy() for _ in pairs]
+    s = rng.integers(0, 2, size=n).astype(np.uint8) if planted else np.zeros(n, np.uint8)
+    oq, om = _oneq_layer(s)
+    return Circuit(n, np.array(pairs, dtype=np.int32).reshape(-1, 2), np.array(mats).reshape(-1, 4, 4),
+                   len(pairs) // 2, oq, om, s, perm, {"family": "permutation_only", "seed": seed})
+
+
+# --- Uniform random operands for MPO microbenchmarks (a batch of independent two-site updates) ---
+
+def random_right_isometry(rng: np.random.Generator, chi_l: int, chi_r: int) -> np.ndarray:
+    """B[chi_l, 4, chi_r] with orthonormal rows (B B^dagger = I), from QR of a Gaussian."""
+    z = rng.standard_normal((4 * chi_r, chi_l)) + 1j * rng.standard_normal((4 * chi_r, chi_l))
+    q, _ = np.linalg.qr(z)
+    return np.ascontiguousarray(q.conj().T.reshape(chi_l, 4, chi_r))
+
+
+def geometric_spectrum(chi: int, scale: float = 64.0) -> np.ndarray:
+    s = np.exp(-np.arange(chi) / scale)
+    return s / np.linalg.norm(s)
+
+
+# --- The named workloads -----------------------------------------------------------------
+
+def workload_line12(seed: int = 0) -> Circuit:
+    """n=12 brickwork mirror, 8 layers per half (44 gates per half), complex128."""
+    return brickwork_mirror(12, 8, seed)
+
+
+def workload_unswap28(seed: int = 0) -> Circuit:
+    """n=28 all-to-all, 200 Haar gates per half, hidden permutation, eps=0.02, complex64 storage."""
+    return hidden_permutation_mirror(28, 200, 0.02, seed, store_complex64=True)
+
+
+def workload_precision36(seed: int = 0) -> Circuit:
+    """n=36 all-to-all, 400 gates per half, hidden permutation, eps=0.03."""
+    return hidden_permutation_mirror(36, 400, 0.03, seed, store_complex64=True)
