@@ -1,0 +1,186 @@
+/*
+ * peaked_mpo.h -- C ABI of the GB300 middle-out MPO contraction library.
+ *
+ * The library computes, on one GPU, the iterative cancellation of a mirrored circuit
+ * C = C_L . C_R into a Matrix Product Operator M (Kremer & Dupuis, "Efficient Classical
+ * Simulation of Heuristic Peaked Quantum Circuits", Algorithm 1):
+ *   - transpile to a line and split at the midpoint (Sec. II.A),
+ *   - absorb the innermost layers of C_L (from the left) and C_R (from the right) into M,
+ *     each gate followed by an SVD with relative cutoff eps (Sec. II.B.1),
+ *   - when size(M) >= tau, unswap: try SWAPs on bonds from the left, right or both sides
+ *     and keep those that lower the bond dimension (Sec. II.B.2; parallel variant App. A.1;
+ *     non-strict acceptance App. A.2), recording M = P_L M~ P_R (Eq. 1),
+ *   - rewire: route the remaining gates with the updated qubit layouts (Sec. II.B.3),
+ *   - apply M to |0...0> and extract the peak / sample / evaluate amplitudes (Sec. II.C).
+ *
+ * Conventions shared by every call:
+ *   - All pointers in signatures are HOST pointers unless a name ends in _dev.  Inputs are
+ *     copied; the caller keeps ownership of every buffer it passes.  Output buffers are
+ *     caller-allocated host memory of the stated size.
+ *   - Complex numbers are stored as interleaved (re, im) float64 pairs.
+ *   - A two-qubit gate on the logical pair (a, b) is a 4x4 row-major matrix in the basis
+ *     index 2*x_a + x_b.  A bitstring is uint8[n] indexed by logical qubit; its integer
+ *     value is sum_q x_q 2^q.
+ *   - Every call returns a pc_status.  0 is success, negative values are errors, positive
+ *     values are warnings.  No C++ exception crosses this boundary.  After an error,
+ *     pc_last_error() on the owning context describes it.
+ *   - Calls on one circuit handle are not thread-safe; distinct handles may be used from
+ *     distinct host threads.  Each circuit owns one CUDA stream.
+ */
+#ifndef PEAKED_MPO_H
+#define PEAKED_MPO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pc_status;
+
+#define PC_OK               0
+#define PC_ERR_INVALID_ARG (-1)   /* bad pointer, size, qubit index or config value      */
+#define PC_ERR_NONUNITARY  (-2)   /* a gate with max|G^dagger G - I| > 1e-6              */
+#define PC_ERR_OOM         (-3)   /* device allocation failed                            */
+#define PC_ERR_NOCONVERGE  (-4)   /* a Jacobi factorisation hit its sweep cap            */
+#define PC_ERR_TIMEOUT     (-5)   /* a bounded device wait gave up                       */
+#define PC_ERR_NOT_PEAKED  (-6)   /* the exact peak search hit its expansion cap         */
+#define PC_ERR_CUDA        (-7)   /* a CUDA runtime call failed                          */
+#define PC_ERR_STATE       (-8)   /* call out of order (e.g. peak before contract)       */
+#define PC_WARN_STALLED     1     /* size(M) stayed >= tau after unswapping (Sec. III.A) */
+
+#define PC_UNSWAP_PARALLEL   0    /* App. A.1: six (side, parity) batches per cycle      */
+#define PC_UNSWAP_SEQUENTIAL 1    /* Algorithm 1: largest available bond, one at a time  */
+#define PC_UNSWAP_OFF        2    /* no unswapping (the plain Middle-MPO attack, Sec. I) */
+
+#define PC_SIDE_LEFT  0           /* out-legs: M <- g M   */
+#define PC_SIDE_RIGHT 1           /* in-legs:  M <- M h   */
+#define PC_SIDE_BOTH  2
+
+typedef struct pc_ctx pc_ctx;
+typedef struct pc_circuit pc_circuit;
+
+/* Hyperparameters of App. A.4 plus the library's own settings. */
+typedef struct pc_config {
+  double eps;                /* SVD cutoff: keep s_k > eps * s_0 (relative, strict)       */
+  int32_t chi_max;           /* hard cap on every bond dimension, 1..4096                 */
+  double tau;                /* size(M) threshold (total tensor elements) for unswapping  */
+  int32_t max_unswap_iter;   /* cap on unswap cycles per stage (paper: 20)                */
+  int32_t accept_equal;      /* 0 strict (paper default), 1 also accept equal dimension   */
+  int32_t unswap_mode;       /* PC_UNSWAP_*                                               */
+  int32_t jacobi_max_sweeps; /* cap on one-sided Jacobi sweeps per factorisation (>= 1)   */
+  int32_t device;            /* CUDA device ordinal                                       */
+} pc_config;
+
+/* Counters filled by pc_contract. */
+typedef struct pc_stats {
+  int64_t n_updates;         /* two-site updates from absorption (gates + routing SWAPs)  */
+  int64_t n_trials;          /* unswap trials evaluated                                   */
+  int64_t n_accepted;        /* unswap trials accepted                                    */
+  int64_t n_stages;          /* outer iterations of Algorithm 1                           */
+  int64_t n_waves;           /* batched launches of independent updates                   */
+  int64_t final_size;        /* size(M) at the end                                        */
+  int32_t max_chi;           /* largest bond dimension seen                               */
+  int32_t stalled;           /* 1 if PC_WARN_STALLED was raised                           */
+  int32_t max_sweeps;        /* largest Jacobi sweep count used by one factorisation      */
+  int32_t pad_;
+  double seconds;            /* host wall time of the call                                */
+} pc_stats;
+
+/* Fills cfg with the paper's defaults except eps/chi_max (1e-10 / 256) and tau (1e6). */
+void pc_default_config(pc_config* cfg);
+
+/* Creates a context on cfg->device.  *out receives the handle; pc_destroy frees it.
+ * Errors: PC_ERR_INVALID_ARG for out-of-range settings, PC_ERR_CUDA. */
+pc_status pc_create(const pc_config* cfg, pc_ctx** out);
+pc_status pc_destroy(pc_ctx* ctx);
+const char* pc_last_error(pc_ctx* ctx);
+
+/* Loads a circuit (Algorithm 1 Require: circuit C on N qubits) and allocates its device MPO
+ * store, initialised to the identity with bond dimension 1 (Algorithm 1, M <- I).
+ *   pairs       int32[n_gates][2]      logical qubits (a, b), a != b, 0 <= a,b < n_qubits
+ *   mats        float64[n_gates][4][4][2]  gate matrices, time order
+ *   split_index gates [0, split) form the earlier half C_R, the rest C_L (Sec. II.A);
+ *               -1 selects n_gates / 2
+ *   oneq_*      n_oneq one-qubit gates applied after every two-qubit gate (e.g. X^s):
+ *               oneq_qubits int32[n_oneq], oneq_mats float64[n_oneq][2][2][2]
+ * Gates are checked for unitarity (PC_ERR_NONUNITARY).  2 <= n_qubits <= 4096. */
+pc_status pc_load_gates(pc_ctx* ctx, int32_t n_qubits, int64_t n_gates, const int32_t* pairs,
+                        const double* mats, int64_t split_index, int64_t n_oneq,
+                        const int32_t* oneq_qubits, const double* oneq_mats, pc_circuit** out);
+pc_status pc_destroy_circuit(pc_circuit* c);
+
+/* Runs Algorithm 1 to the end: every layer absorbed, unswap stages when size(M) >= tau.
+ * Returns PC_WARN_STALLED (> 0) when the progress rule had to force absorption.
+ * stats may be NULL. */
+pc_status pc_contract(pc_circuit* c, pc_stats* stats);
+
+/* One unswap stage (Sec. II.B.2) on the current MPO, in the configured mode.
+ * *n_accepted (may be NULL) receives the number of accepted swaps. */
+pc_status pc_unswap(pc_circuit* c, int32_t* n_accepted);
+
+/* Algorithm 1 Ensure + Sec. II.C: exact argmax_x |<x|C|0>|^2 by best-first search over
+ * prefix marginals.  bits uint8[n]; *p_peak the probability normalised by ||M|0>||^2;
+ * *norm2 (may be NULL) = ||M|0>||^2 (1 for a unitary circuit without truncation).
+ * PC_ERR_NOT_PEAKED if more than max_expansions prefixes had to be expanded. */
+pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, double* p_peak,
+                          double* norm2);
+
+/* Sec. II.C: n_samples bitstrings drawn site by site from the conditionals of M|0>.
+ * The uniforms are u[s][j] = (splitmix64(seed, s*n + j) >> 11) * 2^-53 (site j), and a
+ * site's bit is 1 iff u >= P(0 | prefix).  bits uint8[n_samples][n] (logical order). */
+pc_status pc_sample(pc_circuit* c, int64_t n_samples, uint64_t seed, uint8_t* bits);
+
+/* <x|C|0> for k bitstrings (uint8[k][n] logical order) into amp float64[k][2]. */
+pc_status pc_amplitudes(pc_circuit* c, int64_t k, const uint8_t* bits, double* amp);
+
+/* Inspection.  chi int32[n-1]; layout_l / layout_r int32[n] (logical qubit -> site, the
+ * permutations P_L / P_R of Eq. 1); s float64[cap] the normalised spectrum of one bond. */
+pc_status pc_get_bond_dims(pc_circuit* c, int32_t* chi);
+pc_status pc_get_layouts(pc_circuit* c, int32_t* layout_l, int32_t* layout_r);
+pc_status pc_get_spectrum(pc_circuit* c, int32_t bond, int32_t cap, double* s, int32_t* len);
+
+/* Site tensor B_j as float64[chi_{j-1}][4][chi_j][2] (p = 2*out + in), Hastings/Vidal form:
+ * |M>> = B_0 B_1 ... B_{n-1}, Frobenius norm 1.  dims int32[2] receives (chi_{j-1}, chi_j);
+ * cap is the capacity of out in complex elements. */
+pc_status pc_get_site(pc_circuit* c, int32_t j, int64_t cap, double* out, int32_t* dims);
+
+/* Replaces the MPO with caller-given tensors (for per-kernel tests and microbenchmarks).
+ * chi int32[n+1] with chi[0] = chi[n] = 1 and 1 <= chi[b] <= chi_max otherwise;
+ * sites: the n tensors B_j[chi[j]][4][chi[j+1]] concatenated (complex, interleaved);
+ * lam: the n-1 bond spectra lam_b[chi[b+1]] concatenated.  Layouts reset to identity. */
+pc_status pc_set_state(pc_circuit* c, const int32_t* chi, const double* sites, const double* lam);
+
+/* Applies two-site updates (merge, 16x16 operator, factorise, truncate, split; Sec. II.B.1)
+ * to n_ops bonds that must be pairwise non-adjacent (|b_i - b_k| >= 2), as one batch.
+ *   bonds int32[n_ops], ops float64[n_ops][16][16][2] acting on (p_j, p_{j+1}) with
+ *   p = 2*out + in, row index 4*p_j' + p_{j+1}'.  chi_out int32[n_ops] (may be NULL). */
+pc_status pc_apply_updates(pc_circuit* c, int32_t n_ops, const int32_t* bonds, const double* ops,
+                           int32_t* chi_out);
+
+/* The absorption plan with unswapping off: the sequence of updates the router emits
+ * (Sec. II.A transpilation interleaved with absorption; Algorithm 1 order).  Host-only,
+ * needs no GPU.  rec int32[cap][4] = (side, bond, kind 0 swap / 1 gate, gate index or -1);
+ * *n_rec receives the full count (may exceed cap; then only cap records are written). */
+pc_status pc_plan_routing(int32_t n_qubits, int64_t n_gates, const int32_t* pairs,
+                          int64_t split_index, int64_t cap, int32_t* rec, int64_t* n_rec);
+
+/* The log of pc_contract: plan records int32[cap][5] = (side, bond, kind 0 swap / 1 gate /
+ * 2 accepted unswap, gate or -1, chi after) and unswap records int32[cap][4] = (stage,
+ * iteration, side, bond). */
+pc_status pc_get_plan(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec);
+pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec);
+
+/* Timing of the dominant kernels since the last pc_reset_kernel_timers, measured with CUDA
+ * events on the circuit's stream: per kernel class (0 merge, 1 jacobi, 2 truncate, 3 split,
+ * 4 other) the launch count and total milliseconds; arrays of length 5. */
+pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms);
+pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
+
+/* Library version string. */
+const char* pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEAKED_MPO_H */

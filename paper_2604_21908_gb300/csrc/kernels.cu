@@ -1,0 +1,626 @@
+// CUDA kernels of the middle-out MPO contraction (sm_103a).
+//
+// The hot path of every two-site update (Sec. II.B.1 of the paper: contract the gate with
+// the two MPO site tensors, then an SVD with cutoff eps) is split into
+//   merge      : X = B_j . B_j+1                         (batched complex FP64 GEMM)
+//   gate       : X <- U16 X on the 16-dim (p_j, p_j+1) index, T0 = copy without lambda,
+//                X scaled by lambda_{j-1} row-wise        (gate_apply_kernel)
+//   factorise  : one-sided Jacobi on the rows of X      (jacobi_kernel, cooperative)
+//   truncate   : sort row norms, relative cutoff, chi_max, renormalise (truncate_kernel)
+//   split      : B_j+1 = normalised kept rows (V^dagger), B_j = T0 V / |s| (GEMM)
+// All arithmetic is FP64 (double / double2 complex).
+#include "pc_internal.h"
+
+#include <cstdio>
+
+namespace pc {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // a*b + c
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched complex FP64 GEMM: 64x64 output tile per CTA, K-step 16, 4x4 outputs per thread.
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ descs) {
+  const GemmDesc d = descs[blockIdx.z];
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  if (m0 >= d.M || n0 >= d.N) return;
+  __shared__ double2 As[GBK][GBM];
+  __shared__ double2 Bs[GBK][GBN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int k0 = 0; k0 < d.K; k0 += GBK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + 256 * i;
+      const int r = idx >> 4, c = idx & 15;
+      const int gr = m0 + r, gc = k0 + c;
+      double2 v = make_double2(0.0, 0.0);
+      if (gr < d.M && gc < d.K) {
+        v = d.A[(size_t)gr * d.lda + gc];
+        if (d.row_scale) { const double s = d.row_scale[gr]; v.x *= s; v.y *= s; }
+      }
+      As[c][r] = v;
+    }
+    if (d.opB == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int idx = tid + 256 * i;
+        const int kk = idx >> 6, c = idx & 63;
+        const int gk = k0 + kk, gc = n0 + c;
+        double2 v = make_double2(0.0, 0.0);
+        if (gk < d.K && gc < d.N) v = d.B[(size_t)gk * d.ldb + gc];
+        Bs[kk][c] = v;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int idx = tid + 256 * i;
+        const int nn = idx >> 4, kk = idx & 15;
+        const int gn = n0 + nn, gk = k0 + kk;
+        double2 v = make_double2(0.0, 0.0);
+        if (gk < d.K && gn < d.N) v = conjd(d.B[(size_t)gn * d.ldb + gk]);
+        Bs[kk][nn] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GBK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = m0 + ty + 16 * i;
+    if (gr >= d.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = n0 + tx + 16 * j;
+      if (gc >= d.N) continue;
+      double2 v = make_double2(d.alpha * acc[i][j].x, d.alpha * acc[i][j].y);
+      double2* cp = d.C + (size_t)gr * d.ldc + gc;
+      if (d.accumulate) { const double2 o = *cp; v.x += o.x; v.y += o.y; }
+      *cp = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gate application on the merged two-site tensor.  X[(l,p1), (p2,r)] holds
+// Theta[l, p1, p2, r]; for each (l, r) the 16-vector over P = 4 p1 + p2 is multiplied by U.
+__global__ void __launch_bounds__(256) gate_apply_kernel(const UpdateTask* __restrict__ tasks) {
+  const UpdateTask t = tasks[blockIdx.y];
+  __shared__ double2 U[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) U[i] = t.op[i];
+  __syncthreads();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)t.chi_l * t.chi_r) return;
+  const int l = (int)(idx / t.chi_r), r = (int)(idx % t.chi_r);
+  const int n = t.n;
+  double2 v[16];
+#pragma unroll
+  for (int p1 = 0; p1 < 4; ++p1)
+#pragma unroll
+    for (int p2 = 0; p2 < 4; ++p2) v[4 * p1 + p2] = t.X[(size_t)(4 * l + p1) * n + p2 * t.chi_r + r];
+  const double lam = t.lam_l ? t.lam_l[l] : 1.0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) acc = cfma(U[16 * q + p], v[p], acc);
+    const int row = 4 * l + (q >> 2), col = (q & 3) * t.chi_r + r;
+    t.T0[(size_t)row * n + col] = acc;
+    const size_t xo = t.transposed ? (size_t)col * t.m + row : (size_t)row * n + col;
+    t.X[xo] = make_double2(acc.x * lam, acc.y * lam);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid barrier for the cooperative Jacobi kernel.  The wait is bounded: after about
+// 2^26 polls (seconds) the CTA records an error and the kernel returns.
+__device__ bool grid_barrier(unsigned int* bar, int* err, unsigned int nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == gen) {
+        if (++polls > (1LL << 26) || *(volatile int*)err) { atomicExch(err, 1); break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+
+constexpr int JAC_MAX_TASKS = 256;
+constexpr int JAC_THREADS = 256;
+
+// One-sided (Hestenes) Jacobi on the rows of each task's matrix: rotate pairs of rows until
+// every pair is orthogonal to |<x_a, x_b>| <= tol |x_a| |x_b|, tol = 2 eps_64 sqrt(n).
+// Pairs follow the round-robin (circle) ordering: in round r of a sweep over mp rows,
+// pair 0 = (mp-1, r), pair i = ((r+i) mod (mp-1), (r-i) mod (mp-1)).  Each global iteration
+// runs one round of every unfinished task (tasks of different sizes advance their own
+// sweeps), then all CTAs meet at a grid barrier.  One warp rotates one pair.
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacobiTask* __restrict__ tasks,
+                                                            int ntasks, JacobiStatus* st,
+                                                            int max_sweeps, unsigned int* bar,
+                                                            int* err) {
+  __shared__ int s_off[JAC_MAX_TASKS + 1];
+  __shared__ unsigned char s_done[JAC_MAX_TASKS];
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int t = 0; t < ntasks; ++t) { s_off[t] = off; off += tasks[t].mp >> 1; }
+    s_off[ntasks] = off;
+  }
+  for (int t = threadIdx.x; t < ntasks; t += blockDim.x) s_done[t] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gwarp = blockIdx.x * (JAC_THREADS / 32) + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * (JAC_THREADS / 32);
+  const int total = s_off[ntasks];
+  const double eps64 = 2.220446049250313e-16;
+
+  for (long long g = 0;; ++g) {
+    // Per-task bookkeeping, computed identically by every CTA from global counters that
+    // were final at the last barrier.
+    for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
+      if (s_done[t]) continue;
+      const long long R = tasks[t].mp - 1;
+      const long long s = g / R;
+      const long long r = g - s * R;
+      if (r == 0 && s > 0) {
+        const unsigned int rc = *(volatile unsigned int*)&st[t].rot[(s - 1) % 3];
+        if (rc == 0 || s >= max_sweeps) {
+          s_done[t] = 1;
+          if (blockIdx.x == 0) { st[t].sweeps = (int)s; st[t].converged = rc == 0 ? 1 : 0; }
+          continue;
+        }
+      }
+      if (r == 0 && blockIdx.x == 0) st[t].rot[(s + 1) % 3] = 0u;
+    }
+    __syncthreads();
+    int mine = 1;
+    for (int t = threadIdx.x; t < ntasks; t += blockDim.x) mine &= s_done[t];
+    if (__syncthreads_and(mine)) break;
+
+    for (int item = gwarp; item < total; item += nwarps) {
+      int lo = 0, hi = ntasks - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
+      }
+      const int t = lo;
+      if (s_done[t]) continue;
+      const JacobiTask tk = tasks[t];
+      const int R = tk.mp - 1;
+      const long long s = g / R;
+      const int r = (int)(g - s * R);
+      const int i = item - s_off[t];
+      int a, b;
+      if (i == 0) { a = tk.mp - 1; b = r; }
+      else { a = (r + i) % R; b = (r - i + R) % R; }
+      if (a >= tk.m || b >= tk.m) continue;
+      double2* xa = tk.X + (size_t)a * tk.n;
+      double2* xb = tk.X + (size_t)b * tk.n;
+      double aa = 0.0, bb = 0.0, gr = 0.0, gi = 0.0;
+      for (int k = lane; k < tk.n; k += 32) {
+        const double2 u = xa[k], v = xb[k];
+        aa = fma(u.x, u.x, fma(u.y, u.y, aa));
+        bb = fma(v.x, v.x, fma(v.y, v.y, bb));
+        gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+        gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+      }
+      aa = warp_sum(aa); bb = warp_sum(bb); gr = warp_sum(gr); gi = warp_sum(gi);
+      // rows at the underflow floor are zero for every purpose here
+      if (aa < 1e-280 || bb < 1e-280) continue;
+      const double gabs = hypot(gr, gi);
+      const double tol = 2.0 * eps64 * sqrt((double)tk.n);
+      if (!(gabs > tol * sqrt(aa) * sqrt(bb))) continue;
+      // Real rotation on the phase-adjusted pair: zeta = (b - a) / (2|g|),
+      // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t.
+      const double zeta = (bb - aa) / (2.0 * gabs);
+      double tt;
+      if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
+      else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      const double c = 1.0 / sqrt(1.0 + tt * tt);
+      const double sn = c * tt;
+      const double ex = gr / gabs, ey = -gi / gabs;        // e^{-i phi}
+      const double wx = sn * ex, wy = sn * ey;             // s e^{-i phi}
+      const double zx = c * ex, zy = c * ey;               // c e^{-i phi}
+      for (int k = lane; k < tk.n; k += 32) {
+        const double2 u = xa[k], v = xb[k];
+        double2 na, nb;
+        na.x = c * u.x - (wx * v.x - wy * v.y);
+        na.y = c * u.y - (wx * v.y + wy * v.x);
+        nb.x = sn * u.x + (zx * v.x - zy * v.y);
+        nb.y = sn * u.y + (zx * v.y + zy * v.x);
+        xa[k] = na;
+        xb[k] = nb;
+      }
+      if (tk.Q) {
+        double2* qa = tk.Q + (size_t)a * tk.m;
+        double2* qb = tk.Q + (size_t)b * tk.m;
+        for (int k = lane; k < tk.m; k += 32) {
+          const double2 u = qa[k], v = qb[k];
+          double2 na, nb;
+          na.x = c * u.x - (wx * v.x - wy * v.y);
+          na.y = c * u.y - (wx * v.y + wy * v.x);
+          nb.x = sn * u.x + (zx * v.x - zy * v.y);
+          nb.y = sn * u.y + (zx * v.y + zy * v.x);
+          qa[k] = na;
+          qb[k] = nb;
+        }
+      }
+      if (lane == 0) atomicAdd(&st[t].rot[s % 3], 1u);
+    }
+    if (!grid_barrier(bar, err, gridDim.x)) return;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Truncation: row norms of the orthogonalised matrix are the singular values.  Sort them
+// descending (bitonic, ties by row index), keep s_k > eps * s_0 (at least 1, at most
+// chi_max) and renormalise the kept values to unit 2-norm.
+constexpr int TR_MAX = 4096;
+
+__global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __restrict__ tasks,
+                                                        double eps, int chi_max, int32_t* idx_out,
+                                                        int idx_stride, double* lam_out,
+                                                        double* sraw_out, int lam_stride,
+                                                        TruncOut* out) {
+  extern __shared__ unsigned char smem_raw[];
+  double* sv = reinterpret_cast<double*>(smem_raw);
+  int* id = reinterpret_cast<int*>(sv + TR_MAX);
+  __shared__ double red[32];
+  __shared__ int s_count;
+  const JacobiTask t = tasks[blockIdx.x];
+  int P = 1;
+  while (P < t.m) P <<= 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < P; i += nw) {
+    double acc = 0.0;
+    if (i < t.m) {
+      const double2* row = t.X + (size_t)i * t.n;
+      for (int k = lane; k < t.n; k += 32) acc = fma(row[k].x, row[k].x, fma(row[k].y, row[k].y, acc));
+      acc = warp_sum(acc);
+    }
+    if (lane == 0) { sv[i] = i < t.m ? sqrt(acc) : -1.0; id[i] = i; }
+  }
+  __syncthreads();
+  // bitonic sort, descending by value, ascending by index on ties
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const double a = sv[i], b = sv[ixj];
+          const int ia = id[i], ib = id[ixj];
+          const bool a_first = (a > b) || (a == b && ia < ib);
+          const bool up = (i & k) == 0;
+          if (up ? !a_first : a_first) { sv[i] = b; sv[ixj] = a; id[i] = ib; id[ixj] = ia; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const double s0 = sv[0];
+  const double thr = eps * s0;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < t.m; i += blockDim.x) {
+    const bool keep = sv[i] > thr;
+    const bool next_keep = (i + 1 < t.m) && (sv[i + 1] > thr);
+    if (keep && !next_keep) s_count = i + 1;
+  }
+  __syncthreads();
+  int count = s_count;
+  if (count < 1) count = 1;
+  if (count > chi_max) count = chi_max;
+  // renormalisation: fixed-order tree reduction of the kept squares
+  double part = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) part = fma(sv[i], sv[i], part);
+  part = warp_sum(part);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < nw ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double nrm = sqrt(red[0]);
+  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+    idx_out[(size_t)blockIdx.x * idx_stride + k] = id[k];
+    lam_out[(size_t)blockIdx.x * lam_stride + k] = sv[k] / nrm;
+    sraw_out[(size_t)blockIdx.x * lam_stride + k] = sv[k];
+  }
+  if (threadIdx.x == 0) {
+    TruncOut o;
+    o.count = count;
+    o.m = t.m;
+    o.s0 = s0;
+    o.nrm = nrm;
+    o.s_first_dropped = count < t.m ? sv[count] : 0.0;
+    out[blockIdx.x] = o;
+  }
+}
+
+__global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __restrict__ descs) {
+  const SplitRowsDesc d = descs[blockIdx.y];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)d.count * d.n) return;
+  const int k = (int)(e / d.n), c = (int)(e % d.n);
+  if (d.Q) {
+    const double2 q = d.Q[(size_t)d.idx[k] * d.n + c];
+    d.dst[e] = make_double2(q.x, -q.y);
+  } else {
+    const double inv = 1.0 / d.sraw[k];
+    const double2 v = d.X[(size_t)d.idx[k] * d.n + c];
+    d.dst[e] = make_double2(v.x * inv, v.y * inv);
+  }
+}
+
+__global__ void init_accumulators_kernel(const JacobiTask* __restrict__ tasks) {
+  const JacobiTask t = tasks[blockIdx.y];
+  if (!t.Q) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)t.m * t.m) return;
+  const int i = (int)(e / t.m), j = (int)(e % t.m);
+  t.Q[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void one_site_kernel(double2* B, int chi_l, int chi_r, const double2* g, int side) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)chi_l * 2 * chi_r) return;
+  const int r = (int)(e % chi_r);
+  const int x = (int)((e / chi_r) % 2);      // the leg that is not acted on
+  const int l = (int)(e / (2LL * chi_r));
+  double2 g00 = g[0], g01 = g[1], g10 = g[2], g11 = g[3];
+  if (side == 0) {   // out-legs: new[o] = sum_o' g[o][o'] B[(o', i)]
+    double2* p0 = B + ((size_t)(4 * l + 0 + x)) * chi_r + r;      // o = 0, i = x
+    double2* p1 = B + ((size_t)(4 * l + 2 + x)) * chi_r + r;      // o = 1, i = x
+    const double2 b0 = *p0, b1 = *p1;
+    *p0 = cfma(g01, b1, cmul(g00, b0));
+    *p1 = cfma(g11, b1, cmul(g10, b0));
+  } else {           // in-legs: new[i] = sum_i' B[(o, i')] h[i'][i]
+    double2* p0 = B + ((size_t)(4 * l + 2 * x + 0)) * chi_r + r;
+    double2* p1 = B + ((size_t)(4 * l + 2 * x + 1)) * chi_r + r;
+    const double2 b0 = *p0, b1 = *p1;
+    *p0 = cfma(b1, g10, cmul(b0, g00));
+    *p1 = cfma(b1, g11, cmul(b0, g01));
+  }
+}
+
+// Peak search expansion: both children of one prefix vector, and their marginals.
+__global__ void __launch_bounds__(256) expand_kernel(const double2* v, const double2* Bj, int chi_l,
+                                                    int chi_r, const double2* E, double2* w0,
+                                                    double2* w1, double* marg) {
+  __shared__ double red[2][8];
+  for (int r = threadIdx.x; r < chi_r; r += blockDim.x) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    for (int l = 0; l < chi_l; ++l) {
+      const double2 vl = v[l];
+      a0 = cfma(vl, Bj[(size_t)(4 * l + 0) * chi_r + r], a0);
+      a1 = cfma(vl, Bj[(size_t)(4 * l + 2) * chi_r + r], a1);
+    }
+    w0[r] = a0;
+    w1[r] = a1;
+  }
+  __syncthreads();
+  double m0 = 0.0, m1 = 0.0;
+  for (int c = threadIdx.x; c < chi_r; c += blockDim.x) {
+    double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+    for (int r = 0; r < chi_r; ++r) {
+      const double2 e = E[(size_t)r * chi_r + c];
+      y0 = cfma(w0[r], e, y0);
+      y1 = cfma(w1[r], e, y1);
+    }
+    const double2 c0 = w0[c], c1 = w1[c];
+    m0 += y0.x * c0.x + y0.y * c0.y;
+    m1 += y1.x * c1.x + y1.y * c1.y;
+  }
+  m0 = warp_sum(m0);
+  m1 = warp_sum(m1);
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = m0; red[1][threadIdx.x >> 5] = m1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s0 += red[0][w]; s1 += red[1][w]; }
+    marg[0] = s0;
+    marg[1] = s1;
+  }
+}
+
+__global__ void quadform_rows_kernel(const double2* W, const double2* Y, int rows, int cols, int ld,
+                                     double* out) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  double acc = 0.0;
+  for (int c = lane; c < cols; c += 32) {
+    const double2 y = Y[(size_t)row * ld + c], w = W[(size_t)row * ld + c];
+    acc += y.x * w.x + y.y * w.y;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) out[row] = acc;
+}
+
+__global__ void sample_pick_kernel(const double2* W0, const double2* W1, const double* m0,
+                                   const double* m1, const double* u, int S, int chi, int site,
+                                   int n_sites, double2* Vnext, uint8_t* site_bits) {
+  const int s = blockIdx.x;
+  if (s >= S) return;
+  const double p0 = m0[s], p1 = m1[s];
+  const double P0 = p0 / (p0 + p1);
+  const int bit = u[(size_t)s * n_sites + site] >= P0 ? 1 : 0;
+  const double inv = 1.0 / sqrt(bit ? p1 : p0);
+  const double2* W = bit ? W1 : W0;
+  for (int c = threadIdx.x; c < chi; c += blockDim.x) {
+    const double2 w = W[(size_t)s * chi + c];
+    Vnext[(size_t)s * chi + c] = make_double2(w.x * inv, w.y * inv);
+  }
+  if (threadIdx.x == 0) site_bits[(size_t)s * n_sites + site] = (uint8_t)bit;
+}
+
+__global__ void amp_pick_kernel(const double2* W0, const double2* W1, const uint8_t* site_bits, int K,
+                                int chi, int site, int n_sites, double2* Vnext) {
+  const int k = blockIdx.x;
+  if (k >= K) return;
+  const double2* W = site_bits[(size_t)k * n_sites + site] ? W1 : W0;
+  for (int c = threadIdx.x; c < chi; c += blockDim.x) Vnext[(size_t)k * chi + c] = W[(size_t)k * chi + c];
+}
+
+__global__ void fill_ones_kernel(double2* v, int rows) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) v[i] = make_double2(1.0, 0.0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_gemm(const GemmDesc* d_desc, int batch, int max_m, int max_n, cudaStream_t stream) {
+  if (batch <= 0 || max_m <= 0 || max_n <= 0) return cudaSuccess;
+  dim3 grid((max_n + GBN - 1) / GBN, (max_m + GBM - 1) / GBM, batch);
+  gemm_kernel<<<grid, 256, 0, stream>>>(d_desc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi_l, int max_chi_r,
+                              cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_chi_l * max_chi_r;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  gate_apply_kernel<<<grid, 256, 0, stream>>>(d_tasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_m * max_m;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  init_accumulators_kernel<<<grid, 256, 0, stream>>>(d_tasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                          unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel, JAC_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm > 4) blocks_per_sm = 4;
+    if (blocks_per_sm < 1) return cudaErrorLaunchOutOfResources;
+  }
+  int grid = sm_count * blocks_per_sm;
+  void* args[] = {(void*)&d_tasks, (void*)&ntasks, (void*)&d_status, (void*)&max_sweeps, (void*)&d_bar,
+                  (void*)&d_err};
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+}
+
+cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max, int32_t* d_idx,
+                            int idx_stride, double* d_lam, double* d_sraw, int lam_stride, TruncOut* d_out,
+                            cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = TR_MAX * (sizeof(double) + sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(truncate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  truncate_kernel<<<ntasks, 1024, smem, stream>>>(d_tasks, eps, chi_max, d_idx, idx_stride, d_lam, d_sraw,
+                                                  lam_stride, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_rows(const SplitRowsDesc* d_desc, int ntasks, int max_count, int max_n,
+                              cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_count * max_n;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  split_rows_kernel<<<grid, 256, 0, stream>>>(d_desc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_one_site(double2* B, int chi_l, int chi_r, const double2* g2_dev, int side,
+                            cudaStream_t stream) {
+  const long long cells = (long long)chi_l * 2 * chi_r;
+  one_site_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, stream>>>(B, chi_l, chi_r, g2_dev, side);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const double2* v, const double2* Bj, int chi_l, int chi_r, const double2* E,
+                          double2* w0, double2* w1, double* marg, cudaStream_t stream) {
+  expand_kernel<<<1, 256, 0, stream>>>(v, Bj, chi_l, chi_r, E, w0, w1, marg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quadform_rows(const double2* W, const double2* Y, int rows, int cols, int ld, double* out,
+                                 cudaStream_t stream) {
+  quadform_rows_kernel<<<(rows + 7) / 8, 256, 0, stream>>>(W, Y, rows, cols, ld, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_pick(const double2* W0, const double2* W1, const double* m0, const double* m1,
+                               const double* u, int S, int chi, int site, int n_sites, double2* Vnext,
+                               uint8_t* site_bits, cudaStream_t stream) {
+  sample_pick_kernel<<<S, 128, 0, stream>>>(W0, W1, m0, m1, u, S, chi, site, n_sites, Vnext, site_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amp_pick(const double2* W0, const double2* W1, const uint8_t* site_bits, int K, int chi,
+                            int site, int n_sites, double2* Vnext, cudaStream_t stream) {
+  amp_pick_kernel<<<K, 128, 0, stream>>>(W0, W1, site_bits, K, chi, site, n_sites, Vnext);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ones(double2* v, int rows, cudaStream_t stream) {
+  fill_ones_kernel<<<(rows + 255) / 256, 256, 0, stream>>>(v, rows);
+  return cudaGetLastError();
+}
+
+}  // namespace pc

@@ -1,0 +1,1238 @@
+// Host side of the library: C ABI, device MPO store, router/planner, wave scheduler,
+// unswap driver and the output-MPS queries.  See include/peaked_mpo.h for the contract.
+//
+// The contraction follows Algorithm 1 of Kremer & Dupuis: route each gate to a line
+// (Sec. II.A), absorb the innermost layer of C_L then of C_R (Sec. II.B.1), unswap when
+// size(M) >= tau (Sec. II.B.2, App. A.1), rewire by continuing with the updated layouts
+// (Sec. II.B.3), finally project onto |0...0> (Sec. II.C).
+//
+// The MPO is held as a local-dimension-4 MPS (p = 2*out + in) in Vidal form with Hastings'
+// update: right-canonical site tensors B_j and bond spectra lambda_j.  Updates on disjoint
+// site pairs read and write disjoint data, so the updates of a layer are grouped into
+// waves (as-soon-as-possible over shared sites) and each wave runs as one batch of
+// kernels; the result is identical to applying them one by one.
+#include "../../include/peaked_mpo.h"
+#include "pc_internal.h"
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <queue>
+#include <string>
+#include <vector>
+
+using cplx = std::complex<double>;
+
+namespace {
+
+const char* kVersion = "peaked-mpo-gb300 0.1 (sm_103a, FP64 one-sided Jacobi)";
+
+struct Layout {
+  std::vector<int> pos;    // logical qubit -> site
+  std::vector<int> site;   // site -> logical qubit
+  void reset(int n) {
+    pos.resize(n);
+    site.resize(n);
+    for (int i = 0; i < n; ++i) pos[i] = site[i] = i;
+  }
+  void swap_sites(int j) {
+    const int a = site[j], b = site[j + 1];
+    site[j] = b;
+    site[j + 1] = a;
+    pos[a] = j + 1;
+    pos[b] = j;
+  }
+};
+
+struct PlanOp {       // one two-site update emitted by the router
+  int side;           // PC_SIDE_LEFT / PC_SIDE_RIGHT
+  int bond;
+  int kind;           // 0 routing swap, 1 gate
+  int gate;           // gate index or -1
+};
+
+// 16x16 operator on (p1, p2) with p = 2*o + i for M <- g M h; g acts on (o1, o2) with basis
+// index 2*o1 + o2, h on (i1, i2) as M[o, i] <- sum_i' M[o, i'] h[i', i].  Null means identity.
+void two_site_op(const cplx* g, const cplx* h, cplx* U) {
+  auto G = [&](int r, int c) -> cplx { return g ? g[4 * r + c] : (r == c ? cplx(1, 0) : cplx(0, 0)); };
+  auto H = [&](int r, int c) -> cplx { return h ? h[4 * r + c] : (r == c ? cplx(1, 0) : cplx(0, 0)); };
+  for (int row = 0; row < 16; ++row) {
+    const int p1 = row >> 2, p2 = row & 3;
+    const int o1 = p1 >> 1, i1 = p1 & 1, o2 = p2 >> 1, i2 = p2 & 1;
+    for (int col = 0; col < 16; ++col) {
+      const int q1 = col >> 2, q2 = col & 3;
+      const int a1 = q1 >> 1, b1 = q1 & 1, a2 = q2 >> 1, b2 = q2 & 1;
+      U[16 * row + col] = G(2 * o1 + o2, 2 * a1 + a2) * H(2 * b1 + b2, 2 * i1 + i2);
+    }
+  }
+}
+
+const cplx kSwap4[16] = {1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 1};
+
+void swap_op(int side, cplx* U) {
+  if (side == PC_SIDE_LEFT) two_site_op(kSwap4, nullptr, U);
+  else if (side == PC_SIDE_RIGHT) two_site_op(nullptr, kSwap4, U);
+  else two_site_op(kSwap4, kSwap4, U);
+}
+
+// Greedy as-soon-as-possible layering in absorption order: a gate goes one layer past the
+// last layer that used either of its qubits.
+std::vector<std::vector<int>> make_layers(const std::vector<int>& order, const int32_t* pairs, int n) {
+  std::vector<int> last(n, -1);
+  std::vector<std::vector<int>> layers;
+  for (int g : order) {
+    const int a = pairs[2 * g], b = pairs[2 * g + 1];
+    const int lay = std::max(last[a], last[b]) + 1;
+    if (lay == (int)layers.size()) layers.emplace_back();
+    layers[lay].push_back(g);
+    last[a] = last[b] = lay;
+  }
+  return layers;
+}
+
+// Routes one gate of one side: the first-listed qubit moves one site at a time toward the
+// second (a SWAP update per step), then the gate is applied on the bond they share.
+void route_gate(int side, int g, const int32_t* pairs, Layout& lay, std::vector<PlanOp>& out) {
+  const int a = pairs[2 * g], b = pairs[2 * g + 1];
+  int p = lay.pos[a];
+  const int q = lay.pos[b];
+  while (std::abs(p - q) > 1) {
+    const int j = p < q ? p : p - 1;
+    out.push_back({side, j, 0, -1});
+    lay.swap_sites(j);
+    p = lay.pos[a];
+  }
+  out.push_back({side, std::min(p, q), 1, g});
+}
+
+inline double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct pc_ctx {
+  pc_config cfg;
+  int sm_count = 0;
+  std::string last_error;
+};
+
+struct pc_circuit {
+  pc_ctx* ctx = nullptr;
+  int n = 0;
+  int chi_max = 0;
+  int max_tasks = 0;
+  std::vector<int32_t> pairs;
+  std::vector<cplx> mats;
+  int64_t split = 0;
+  std::vector<int32_t> oneq_q;
+  std::vector<cplx> oneq_m;
+  std::vector<std::vector<int>> left_layers, right_layers;
+  size_t lcur = 0, rcur = 0;
+  bool oneq_done = true;
+  Layout lay[2];
+  std::vector<int> chi;           // chi[k], k = 0..n: left bond of site k; chi[0] = chi[n] = 1
+  std::vector<size_t> site_off;   // element offset of each site slot
+  cudaStream_t stream = nullptr;
+  // device memory
+  double2* d_sites = nullptr;
+  double* d_lam = nullptr;        // bond b spectrum at d_lam + b * chi_max
+  double2* d_X = nullptr;
+  double2* d_T0 = nullptr;
+  double2* d_Q = nullptr;         // Jacobi accumulators (transposed path)
+  size_t scratch_elems = 0;       // per task
+  double2* d_ops = nullptr;
+  pc::UpdateTask* d_tasks = nullptr;
+  pc::JacobiTask* d_jtasks = nullptr;
+  pc::GemmDesc* d_gemm = nullptr;
+  pc::GemmDesc* d_gemm2 = nullptr;
+  pc::SplitRowsDesc* d_split = nullptr;
+  pc::JacobiStatus* d_jst = nullptr;
+  pc::TruncOut* d_tout = nullptr;
+  int32_t* d_idx = nullptr;
+  double* d_lamnew = nullptr;
+  double* d_sraw = nullptr;
+  unsigned int* d_bar = nullptr;
+  int* d_err = nullptr;
+  double2* d_g2 = nullptr;
+  // pinned staging
+  cplx* h_ops = nullptr;
+  pc::UpdateTask* h_tasks = nullptr;
+  pc::JacobiTask* h_jtasks = nullptr;
+  pc::GemmDesc* h_gemm = nullptr;
+  pc::GemmDesc* h_gemm2 = nullptr;
+  pc::SplitRowsDesc* h_split = nullptr;
+  pc::JacobiStatus* h_jst = nullptr;
+  pc::TruncOut* h_tout = nullptr;
+  int* h_err = nullptr;
+  // output MPS (environments)
+  bool projected = false;
+  double2* d_env = nullptr;
+  std::vector<size_t> env_off;
+  double norm2 = 0.0;
+  // logs and stats
+  std::vector<std::array<int32_t, 5>> plan_log;
+  std::vector<std::array<int32_t, 4>> unswap_log;
+  pc_stats stats{};
+  int stage = 0;
+  // kernel timers
+  bool timing = false;
+  cudaEvent_t ev[6] = {};
+  int64_t t_launch[5] = {};
+  double t_ms[5] = {};
+};
+
+namespace {
+
+pc_status fail(pc_ctx* ctx, pc_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                      \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA,             \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+double2* site_ptr(pc_circuit* c, int j) { return c->d_sites + c->site_off[j]; }
+double* lam_ptr(pc_circuit* c, int b) { return c->d_lam + (size_t)b * c->chi_max; }
+
+int64_t mpo_size(const pc_circuit* c) {
+  int64_t s = 0;
+  for (int j = 0; j < c->n; ++j) s += (int64_t)c->chi[j] * 4 * c->chi[j + 1];
+  return s;
+}
+
+int max_bond(const pc_circuit* c) {
+  int m = 1;
+  for (int k = 1; k < c->n; ++k) m = std::max(m, c->chi[k]);
+  return m;
+}
+
+void free_circuit(pc_circuit* c) {
+  if (!c) return;
+  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_ops);
+  cudaFree(c->d_tasks); cudaFree(c->d_jtasks); cudaFree(c->d_gemm); cudaFree(c->d_gemm2);
+  cudaFree(c->d_split); cudaFree(c->d_jst); cudaFree(c->d_tout); cudaFree(c->d_idx);
+  cudaFree(c->d_lamnew); cudaFree(c->d_sraw); cudaFree(c->d_bar); cudaFree(c->d_err); cudaFree(c->d_g2);
+  cudaFree(c->d_env);
+  cudaFreeHost(c->h_ops); cudaFreeHost(c->h_tasks); cudaFreeHost(c->h_jtasks); cudaFreeHost(c->h_gemm);
+  cudaFreeHost(c->h_gemm2); cudaFreeHost(c->h_split); cudaFreeHost(c->h_jst); cudaFreeHost(c->h_tout);
+  cudaFreeHost(c->h_err);
+  for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+pc_status alloc_circuit(pc_circuit* c) {
+  pc_ctx* ctx = c->ctx;
+  const int n = c->n, X = c->chi_max;
+  c->chi.assign(n + 1, 1);
+  c->site_off.resize(n + 1);
+  size_t off = 0;
+  for (int j = 0; j < n; ++j) {
+    c->site_off[j] = off;
+    const size_t cl = j == 0 ? 1 : X, cr = j == n - 1 ? 1 : X;
+    off += cl * 4 * cr;
+  }
+  c->site_off[n] = off;
+  c->max_tasks = std::max(1, std::min(n / 2, 32));
+  c->scratch_elems = (size_t)(4 * X) * (4 * X);
+  const int T = c->max_tasks;
+  CUDA_TRY(ctx, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_sites, off * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_lam, (size_t)std::max(1, n - 1) * X * sizeof(double)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_X, (size_t)T * c->scratch_elems * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_T0, (size_t)T * c->scratch_elems * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_Q, (size_t)T * c->scratch_elems * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_ops, (size_t)T * 256 * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_tasks, T * sizeof(pc::UpdateTask)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_jtasks, T * sizeof(pc::JacobiTask)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_gemm, T * sizeof(pc::GemmDesc)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_gemm2, T * sizeof(pc::GemmDesc)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_split, T * sizeof(pc::SplitRowsDesc)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_jst, T * sizeof(pc::JacobiStatus)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_tout, T * sizeof(pc::TruncOut)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_idx, (size_t)T * 4 * X * sizeof(int32_t)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_lamnew, (size_t)T * 4 * X * sizeof(double)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_sraw, (size_t)T * 4 * X * sizeof(double)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_bar, 2 * sizeof(unsigned int)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_err, sizeof(int)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_g2, 4 * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_ops, (size_t)T * 256 * sizeof(cplx)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_tasks, T * sizeof(pc::UpdateTask)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_jtasks, T * sizeof(pc::JacobiTask)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_gemm, T * sizeof(pc::GemmDesc)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_gemm2, T * sizeof(pc::GemmDesc)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_split, T * sizeof(pc::SplitRowsDesc)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_jst, T * sizeof(pc::JacobiStatus)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_tout, T * sizeof(pc::TruncOut)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_err, sizeof(int)));
+  for (auto& e : c->ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+  return PC_OK;
+}
+
+// Identity MPO (Algorithm 1: M <- I, bond dimension 1): B_j[0, p, 0] = delta_{o,i} / sqrt 2.
+pc_status reset_identity(pc_circuit* c) {
+  std::vector<double2> h(4 * c->n);
+  const double r = 1.0 / std::sqrt(2.0);
+  for (int j = 0; j < c->n; ++j) {
+    h[4 * j + 0] = make_double2(r, 0.0);
+    h[4 * j + 1] = make_double2(0.0, 0.0);
+    h[4 * j + 2] = make_double2(0.0, 0.0);
+    h[4 * j + 3] = make_double2(r, 0.0);
+  }
+  std::fill(c->chi.begin(), c->chi.end(), 1);
+  for (int j = 0; j < c->n; ++j)
+    CUDA_TRY(c->ctx, cudaMemcpyAsync(site_ptr(c, j), &h[4 * j], 4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> ones(std::max(1, c->n - 1), 1.0);
+  for (int b = 0; b + 1 < c->n; ++b)
+    CUDA_TRY(c->ctx, cudaMemcpyAsync(lam_ptr(c, b), &ones[b], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+  c->lay[0].reset(c->n);
+  c->lay[1].reset(c->n);
+  c->projected = false;
+  return PC_OK;
+}
+
+void timer_mark(pc_circuit* c, int i) {
+  if (c->timing) cudaEventRecord(c->ev[i], c->stream);
+}
+
+// One wave: factorise every task (merge, gate, Jacobi, truncate), then split the ones that
+// are committed.  `accept` (may be null) decides per task from its count; counts returned.
+struct WaveItem {
+  int bond;
+  cplx op[256];
+};
+
+pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vector<int>& counts,
+                   const std::vector<int>* commit_mask_in, bool decide_by_accept, bool accept_equal,
+                   std::vector<int>* accepted_out) {
+  pc_ctx* ctx = c->ctx;
+  const int T = (int)items.size();
+  counts.assign(T, 0);
+  if (T == 0) return PC_OK;
+  if (T > c->max_tasks) return fail(ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
+  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0;
+  for (int t = 0; t < T; ++t) {
+    const int j = items[t].bond;
+    const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
+    std::memcpy(c->h_ops + (size_t)t * 256, items[t].op, 256 * sizeof(cplx));
+    pc::UpdateTask& u = c->h_tasks[t];
+    u.Bl = site_ptr(c, j);
+    u.Br = site_ptr(c, j + 1);
+    u.lam_l = j > 0 ? lam_ptr(c, j - 1) : nullptr;
+    u.op = reinterpret_cast<const double2*>(c->d_ops) + (size_t)t * 256;
+    u.X = c->d_X + (size_t)t * c->scratch_elems;
+    u.T0 = c->d_T0 + (size_t)t * c->scratch_elems;
+    u.chi_l = cl; u.chi_m = cm; u.chi_r = cr;
+    u.m = 4 * cl; u.n = 4 * cr;
+    u.transposed = u.m > u.n ? 1 : 0;
+    pc::GemmDesc& g = c->h_gemm[t];
+    g.A = u.Bl; g.B = u.Br; g.C = u.X; g.row_scale = nullptr;
+    g.M = 4 * cl; g.N = 4 * cr; g.K = cm;
+    g.lda = cm; g.ldb = 4 * cr; g.ldc = 4 * cr;
+    g.opB = 0; g.accumulate = 0; g.alpha = 1.0;
+    // The Jacobi orthogonalises min(m, n) vectors: the rows of X, or for a tall bond matrix
+    // its columns, with the rotations accumulated into Q (the right singular vectors).
+    pc::JacobiTask& jt = c->h_jtasks[t];
+    jt.X = u.X;
+    jt.Q = u.transposed ? c->d_Q + (size_t)t * c->scratch_elems : nullptr;
+    jt.m = u.transposed ? u.n : u.m;
+    jt.n = u.transposed ? u.m : u.n;
+    jt.mp = jt.m + (jt.m & 1);
+    jt.pad_ = 0;
+    max_m = std::max(max_m, u.m); max_n = std::max(max_n, u.n);
+    max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
+  }
+  cudaStream_t s = c->stream;
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_ops, c->h_ops, (size_t)T * 256 * sizeof(cplx), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_tasks, c->h_tasks, T * sizeof(pc::UpdateTask), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
+  CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
+  CUDA_TRY(ctx, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+  timer_mark(c, 0);
+  CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, T, max_m, max_n, s));
+  CUDA_TRY(ctx, pc::launch_gate_apply(c->d_tasks, T, max_cl, max_cr, s));
+  CUDA_TRY(ctx, pc::launch_init_accumulators(c->d_jtasks, T, max_n, s));
+  timer_mark(c, 1);
+  CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
+                                  ctx->sm_count, s));
+  timer_mark(c, 2);
+  const int stride = 4 * c->chi_max;
+  CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,
+                                    c->d_sraw, stride, c->d_tout, s));
+  timer_mark(c, 3);
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_tout, c->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_jst, c->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (c->timing) {
+    float a = 0, b = 0, d = 0;
+    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+    c->t_ms[0] += a; c->t_ms[1] += b; c->t_ms[2] += d;
+    c->t_launch[0] += 1; c->t_launch[1] += 1; c->t_launch[2] += 1;
+  }
+  if (*c->h_err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+  for (int t = 0; t < T; ++t) {
+    counts[t] = c->h_tout[t].count;
+    c->stats.max_sweeps = std::max(c->stats.max_sweeps, c->h_jst[t].sweeps);
+    if (!c->h_jst[t].converged)
+      return fail(ctx, PC_ERR_NOCONVERGE, "one-sided Jacobi reached the sweep cap on bond " + std::to_string(items[t].bond));
+  }
+  // commit decisions
+  std::vector<int> commit(T, 1);
+  if (commit_mask_in) commit = *commit_mask_in;
+  if (decide_by_accept) {
+    for (int t = 0; t < T; ++t) {
+      const int old = c->chi[items[t].bond + 1];
+      commit[t] = accept_equal ? (counts[t] <= old) : (counts[t] < old);
+    }
+  }
+  if (accepted_out) *accepted_out = commit;
+  int nc = 0, max_cnt = 0, max_nn = 0, max_mm = 0;
+  for (int t = 0; t < T; ++t) {
+    if (!commit[t]) continue;
+    const int j = items[t].bond;
+    const pc::UpdateTask& u = c->h_tasks[t];
+    const int cnt = counts[t];
+    pc::SplitRowsDesc& sd = c->h_split[nc];
+    sd.X = u.X;
+    sd.Q = u.transposed ? c->h_jtasks[t].Q : nullptr;
+    sd.dst = site_ptr(c, j + 1);
+    sd.idx = c->d_idx + (size_t)t * stride;
+    sd.sraw = c->d_sraw + (size_t)t * stride;
+    sd.count = cnt;
+    sd.n = u.n;
+    pc::GemmDesc& g = c->h_gemm2[nc];
+    g.A = u.T0; g.B = sd.dst; g.C = site_ptr(c, j); g.row_scale = nullptr;
+    g.M = u.m; g.N = cnt; g.K = u.n;
+    g.lda = u.n; g.ldb = u.n; g.ldc = cnt;
+    g.opB = 1; g.accumulate = 0; g.alpha = 1.0 / c->h_tout[t].nrm;
+    max_cnt = std::max(max_cnt, cnt); max_nn = std::max(max_nn, u.n); max_mm = std::max(max_mm, u.m);
+    ++nc;
+  }
+  if (nc > 0) {
+    timer_mark(c, 4);
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_split, c->h_split, nc * sizeof(pc::SplitRowsDesc), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm2, c->h_gemm2, nc * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, pc::launch_split_rows(c->d_split, nc, max_cnt, max_nn, s));
+    CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm2, nc, max_mm, max_cnt, s));
+    for (int t = 0; t < T; ++t) {
+      if (!commit[t]) continue;
+      const int j = items[t].bond;
+      CUDA_TRY(ctx, cudaMemcpyAsync(lam_ptr(c, j), c->d_lamnew + (size_t)t * stride, counts[t] * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+      c->chi[j + 1] = counts[t];
+    }
+    timer_mark(c, 5);
+    if (c->timing) {
+      // the split is measured at the next synchronisation point
+      CUDA_TRY(ctx, cudaStreamSynchronize(s));
+      float e = 0;
+      cudaEventElapsedTime(&e, c->ev[4], c->ev[5]);
+      c->t_ms[3] += e;
+      c->t_launch[3] += 1;
+    }
+  }
+  c->stats.max_chi = std::max(c->stats.max_chi, max_bond(c));
+  c->stats.n_waves += 1;
+  c->projected = false;
+  return PC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// The planner proper.  Orientation is resolved at planning time (the layout right after a
+// gate's own routing), so a planned op carries its final 16x16 operator.
+namespace {
+
+struct ResolvedOp {
+  int side, bond, kind, gate;
+  bool reversed;
+};
+
+std::vector<ResolvedOp> plan_layer(int side, const std::vector<int>& layer, const int32_t* pairs, Layout& lay) {
+  std::vector<ResolvedOp> out;
+  for (int g : layer) {
+    std::vector<PlanOp> one;
+    route_gate(side, g, pairs, lay, one);
+    for (const PlanOp& op : one) {
+      bool rev = false;
+      if (op.kind == 1) rev = lay.pos[pairs[2 * g]] > lay.pos[pairs[2 * g + 1]];
+      out.push_back({op.side, op.bond, op.kind, op.gate, rev});
+    }
+  }
+  return out;
+}
+
+void build_op(pc_circuit* c, const ResolvedOp& op, cplx* U) {
+  if (op.kind == 0) { swap_op(op.side, U); return; }
+  cplx g[16];
+  const cplx* m = &c->mats[(size_t)op.gate * 16];
+  for (int r = 0; r < 4; ++r)
+    for (int col = 0; col < 4; ++col) {
+      const int rr = op.reversed ? ((r & 1) << 1 | (r >> 1)) : r;
+      const int cc = op.reversed ? ((col & 1) << 1 | (col >> 1)) : col;
+      g[4 * r + col] = m[4 * rr + cc];
+    }
+  if (op.side == PC_SIDE_LEFT) two_site_op(g, nullptr, U);
+  else two_site_op(nullptr, g, U);
+}
+
+pc_status apply_resolved(pc_circuit* c, const std::vector<ResolvedOp>& ops) {
+  const int n = c->n;
+  std::vector<int> wave_of(ops.size());
+  std::vector<int> last(n, -1);
+  int nw = 0;
+  for (size_t u = 0; u < ops.size(); ++u) {
+    const int j = ops[u].bond;
+    const int w = std::max(last[j], last[j + 1]) + 1;
+    wave_of[u] = w;
+    last[j] = last[j + 1] = w;
+    nw = std::max(nw, w + 1);
+  }
+  std::vector<std::vector<size_t>> waves(nw);
+  for (size_t u = 0; u < ops.size(); ++u) waves[wave_of[u]].push_back(u);
+  std::vector<WaveItem> items;
+  std::vector<int> counts;
+  std::vector<int> chi_after(ops.size(), 0);
+  for (int w = 0; w < nw; ++w) {
+    const auto& idx = waves[w];
+    for (size_t base = 0; base < idx.size(); base += c->max_tasks) {
+      const size_t cnt = std::min(idx.size() - base, (size_t)c->max_tasks);
+      items.resize(cnt);
+      for (size_t k = 0; k < cnt; ++k) {
+        items[k].bond = ops[idx[base + k]].bond;
+        build_op(c, ops[idx[base + k]], items[k].op);
+      }
+      pc_status st = run_wave(c, items, counts, nullptr, false, false, nullptr);
+      if (st != PC_OK) return st;
+      for (size_t k = 0; k < cnt; ++k) chi_after[idx[base + k]] = counts[k];
+    }
+  }
+  for (size_t u = 0; u < ops.size(); ++u)
+    c->plan_log.push_back({ops[u].side, ops[u].bond, ops[u].kind, ops[u].gate, chi_after[u]});
+  c->stats.n_updates += (int64_t)ops.size();
+  return PC_OK;
+}
+
+pc_status apply_oneq_layer(pc_circuit* c) {
+  for (size_t k = 0; k < c->oneq_q.size(); ++k) {
+    const int j = c->lay[PC_SIDE_LEFT].pos[c->oneq_q[k]];
+    CUDA_TRY(c->ctx, cudaMemcpyAsync(c->d_g2, &c->oneq_m[4 * k], 4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c->ctx, pc::launch_one_site(site_ptr(c, j), c->chi[j], c->chi[j + 1], c->d_g2, PC_SIDE_LEFT, c->stream));
+    CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+  }
+  c->projected = false;
+  return PC_OK;
+}
+
+bool layers_remain(const pc_circuit* c) {
+  return c->lcur < c->left_layers.size() || !c->oneq_done || c->rcur < c->right_layers.size();
+}
+
+pc_status absorb_layer_pair(pc_circuit* c) {
+  std::vector<ResolvedOp> ops;
+  bool do_oneq = false;
+  if (c->lcur < c->left_layers.size()) {
+    auto l = plan_layer(PC_SIDE_LEFT, c->left_layers[c->lcur], c->pairs.data(), c->lay[PC_SIDE_LEFT]);
+    ops.insert(ops.end(), l.begin(), l.end());
+    c->lcur++;
+  } else if (!c->oneq_done) {
+    do_oneq = true;
+  }
+  if (c->rcur < c->right_layers.size()) {
+    auto r = plan_layer(PC_SIDE_RIGHT, c->right_layers[c->rcur], c->pairs.data(), c->lay[PC_SIDE_RIGHT]);
+    ops.insert(ops.end(), r.begin(), r.end());
+    c->rcur++;
+  }
+  // The one-qubit layer sits outermost on the left: apply it after the left's (empty) layer
+  // and before the right's layer, exactly as absorbed in order; it commutes with the right
+  // layer's updates only if they avoid its sites, so keep the order: left, one-qubit, right.
+  if (do_oneq) {
+    pc_status st = apply_oneq_layer(c);
+    if (st != PC_OK) return st;
+    c->oneq_done = true;
+  }
+  return apply_resolved(c, ops);
+}
+
+// App. A.1 parallel swap selection.
+pc_status unswap_parallel(pc_circuit* c, int* n_acc) {
+  pc_ctx* ctx = c->ctx;
+  const int order[6][2] = {{PC_SIDE_BOTH, 0}, {PC_SIDE_BOTH, 1}, {PC_SIDE_LEFT, 0},
+                           {PC_SIDE_LEFT, 1}, {PC_SIDE_RIGHT, 0}, {PC_SIDE_RIGHT, 1}};
+  int total = 0;
+  std::vector<WaveItem> items;
+  std::vector<int> counts, acc;
+  for (int it = 0; it < ctx->cfg.max_unswap_iter; ++it) {
+    bool any = false;
+    for (const auto& sp : order) {
+      const int side = sp[0], parity = sp[1];
+      std::vector<int> bonds;
+      for (int b = parity; b + 1 < c->n; b += 2) bonds.push_back(b);
+      for (size_t base = 0; base < bonds.size(); base += c->max_tasks) {
+        const size_t cnt = std::min(bonds.size() - base, (size_t)c->max_tasks);
+        items.resize(cnt);
+        for (size_t k = 0; k < cnt; ++k) {
+          items[k].bond = bonds[base + k];
+          swap_op(side, items[k].op);
+        }
+        pc_status st = run_wave(c, items, counts, nullptr, true, ctx->cfg.accept_equal != 0, &acc);
+        if (st != PC_OK) return st;
+        c->stats.n_trials += (int64_t)cnt;
+        for (size_t k = 0; k < cnt; ++k) {
+          if (!acc[k]) continue;
+          const int b = bonds[base + k];
+          if (side == PC_SIDE_LEFT || side == PC_SIDE_BOTH) c->lay[PC_SIDE_LEFT].swap_sites(b);
+          if (side == PC_SIDE_RIGHT || side == PC_SIDE_BOTH) c->lay[PC_SIDE_RIGHT].swap_sites(b);
+          c->unswap_log.push_back({c->stage, it, side, b});
+          c->plan_log.push_back({side, b, 2, -1, counts[k]});
+          any = true;
+          ++total;
+        }
+      }
+    }
+    if (!any) break;
+  }
+  c->stats.n_accepted += total;
+  if (n_acc) *n_acc = total;
+  return PC_OK;
+}
+
+// Algorithm 1 sequential unswapping: largest available bond (smallest index on ties), the
+// three sides tried as one wave (the trials share sites, so they run as three separate
+// one-task waves that do not commit), best = smallest count, ties in side order.
+pc_status unswap_sequential(pc_circuit* c, int* n_acc) {
+  pc_ctx* ctx = c->ctx;
+  const int nb = c->n - 1;
+  std::vector<char> avail(nb, 1);
+  int navail = nb, total = 0;
+  const long long cap = (long long)ctx->cfg.max_unswap_iter * std::max(c->n, 1) * 4;
+  long long steps = 0;
+  std::vector<WaveItem> items(1);
+  std::vector<int> counts, none(1, 0);
+  while (navail > 0 && steps < cap) {
+    ++steps;
+    int i = -1;
+    for (int b = 0; b < nb; ++b)
+      if (avail[b] && (i < 0 || c->chi[b + 1] > c->chi[i + 1])) i = b;
+    int best_cnt = 1 << 30, best_side = -1;
+    for (int side = 0; side < 3; ++side) {
+      items[0].bond = i;
+      swap_op(side, items[0].op);
+      pc_status st = run_wave(c, items, counts, &none, false, false, nullptr);
+      if (st != PC_OK) return st;
+      c->stats.n_trials += 1;
+      if (counts[0] < best_cnt) { best_cnt = counts[0]; best_side = side; }
+    }
+    const int old = c->chi[i + 1];
+    const bool ok = ctx->cfg.accept_equal ? best_cnt <= old : best_cnt < old;
+    if (ok) {
+      // recompute the winning trial and commit it
+      items[0].bond = i;
+      swap_op(best_side, items[0].op);
+      std::vector<int> one(1, 1);
+      pc_status st = run_wave(c, items, counts, &one, false, false, nullptr);
+      if (st != PC_OK) return st;
+      if (best_side == PC_SIDE_LEFT || best_side == PC_SIDE_BOTH) c->lay[PC_SIDE_LEFT].swap_sites(i);
+      if (best_side == PC_SIDE_RIGHT || best_side == PC_SIDE_BOTH) c->lay[PC_SIDE_RIGHT].swap_sites(i);
+      c->unswap_log.push_back({c->stage, (int)(steps - 1), best_side, i});
+      c->plan_log.push_back({best_side, i, 2, -1, counts[0]});
+      ++total;
+      avail[i] = 0; --navail;
+      for (int nbnd : {i - 1, i + 1})
+        if (nbnd >= 0 && nbnd < nb && !avail[nbnd]) { avail[nbnd] = 1; ++navail; }
+    } else {
+      avail[i] = 0; --navail;
+    }
+  }
+  c->stats.n_accepted += total;
+  if (n_acc) *n_acc = total;
+  return PC_OK;
+}
+
+pc_status unswap_stage(pc_circuit* c, int* n_acc) {
+  if (n_acc) *n_acc = 0;
+  if (c->n < 2) return PC_OK;
+  switch (c->ctx->cfg.unswap_mode) {
+    case PC_UNSWAP_PARALLEL: return unswap_parallel(c, n_acc);
+    case PC_UNSWAP_SEQUENTIAL: return unswap_sequential(c, n_acc);
+    default: return PC_OK;
+  }
+}
+
+// Right environments of M|0>: env_n = 1, env_j = sum_s A_j^s env_{j+1} A_j^s^dagger with
+// A_j^s = B_j[:, 2 s, :] (in-leg set to 0).
+pc_status project(pc_circuit* c) {
+  if (c->projected) return PC_OK;
+  pc_ctx* ctx = c->ctx;
+  const int n = c->n;
+  c->env_off.assign(n + 1, 0);
+  size_t off = 0;
+  for (int j = 0; j <= n; ++j) { c->env_off[j] = off; off += (size_t)c->chi[j] * c->chi[j]; }
+  cudaFree(c->d_env);
+  c->d_env = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&c->d_env, (off + (size_t)c->chi_max * c->chi_max) * sizeof(double2)));
+  double2* tmp = c->d_env + off;   // chi_l x chi_r scratch
+  const double2 one = make_double2(1.0, 0.0);
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_env + c->env_off[n], &one, sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  for (int j = n - 1; j >= 0; --j) {
+    const int cl = c->chi[j], cr = c->chi[j + 1];
+    for (int sgm = 0; sgm < 2; ++sgm) {
+      pc::GemmDesc g1{}, g2{};
+      g1.A = site_ptr(c, j) + 2 * sgm * cr; g1.lda = 4 * cr;
+      g1.B = c->d_env + c->env_off[j + 1]; g1.ldb = cr;
+      g1.C = tmp; g1.ldc = cr;
+      g1.M = cl; g1.N = cr; g1.K = cr; g1.opB = 0; g1.accumulate = 0; g1.alpha = 1.0;
+      g2.A = tmp; g2.lda = cr;
+      g2.B = site_ptr(c, j) + 2 * sgm * cr; g2.ldb = 4 * cr;
+      g2.C = c->d_env + c->env_off[j]; g2.ldc = cl;
+      g2.M = cl; g2.N = cl; g2.K = cr; g2.opB = 1; g2.accumulate = sgm; g2.alpha = 1.0;
+      c->h_gemm[0] = g1;
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cr, c->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+      c->h_gemm[0] = g2;
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cl, c->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+    }
+  }
+  double2 z;
+  CUDA_TRY(ctx, cudaMemcpy(&z, c->d_env + c->env_off[0], sizeof(double2), cudaMemcpyDeviceToHost));
+  c->norm2 = z.x;
+  c->projected = true;
+  return PC_OK;
+}
+
+pc_status check_circuit(pc_circuit* c) {
+  if (!c || !c->ctx) return PC_ERR_INVALID_ARG;
+  return PC_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+extern "C" {
+
+const char* pc_version(void) { return kVersion; }
+
+void pc_default_config(pc_config* cfg) {
+  if (!cfg) return;
+  cfg->eps = 1e-10;
+  cfg->chi_max = 256;
+  cfg->tau = 1e6;
+  cfg->max_unswap_iter = 20;
+  cfg->accept_equal = 0;
+  cfg->unswap_mode = PC_UNSWAP_PARALLEL;
+  cfg->jacobi_max_sweeps = 60;
+  cfg->device = 0;
+}
+
+pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
+  if (!cfg || !out) return PC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(cfg->eps >= 0.0) || cfg->chi_max < 1 || cfg->chi_max > 1024 || !(cfg->tau > 0.0) ||
+      cfg->max_unswap_iter < 0 || cfg->jacobi_max_sweeps < 1 || cfg->unswap_mode < 0 || cfg->unswap_mode > 2)
+    return PC_ERR_INVALID_ARG;
+  auto* ctx = new pc_ctx();
+  ctx->cfg = *cfg;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return PC_ERR_CUDA;
+  }
+  *out = ctx;
+  return PC_OK;
+}
+
+pc_status pc_destroy(pc_ctx* ctx) {
+  delete ctx;
+  return PC_OK;
+}
+
+const char* pc_last_error(pc_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+pc_status pc_load_gates(pc_ctx* ctx, int32_t n_qubits, int64_t n_gates, const int32_t* pairs, const double* mats,
+                        int64_t split_index, int64_t n_oneq, const int32_t* oneq_qubits, const double* oneq_mats,
+                        pc_circuit** out) {
+  if (!ctx || !out) return PC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_qubits < 2 || n_qubits > 4096 || n_gates < 0 || n_oneq < 0 || (n_gates > 0 && (!pairs || !mats)) ||
+      (n_oneq > 0 && (!oneq_qubits || !oneq_mats)))
+    return fail(ctx, PC_ERR_INVALID_ARG, "bad sizes or null pointers");
+  if (split_index < 0) split_index = n_gates / 2;
+  if (split_index > n_gates) return fail(ctx, PC_ERR_INVALID_ARG, "split_index beyond the gate list");
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
+  auto* c = new pc_circuit();
+  c->ctx = ctx;
+  c->n = n_qubits;
+  c->chi_max = ctx->cfg.chi_max;
+  c->pairs.assign(pairs, pairs + 2 * n_gates);
+  c->mats.resize(16 * n_gates);
+  for (int64_t g = 0; g < n_gates; ++g) {
+    const int a = pairs[2 * g], b = pairs[2 * g + 1];
+    if (a < 0 || b < 0 || a >= n_qubits || b >= n_qubits || a == b) {
+      delete c;
+      return fail(ctx, PC_ERR_INVALID_ARG, "gate " + std::to_string(g) + " has a bad qubit pair");
+    }
+    for (int k = 0; k < 16; ++k) c->mats[16 * g + k] = cplx(mats[32 * g + 2 * k], mats[32 * g + 2 * k + 1]);
+    double dev = 0.0;
+    for (int r = 0; r < 4; ++r)
+      for (int col = 0; col < 4; ++col) {
+        cplx acc = 0;
+        for (int k = 0; k < 4; ++k) acc += std::conj(c->mats[16 * g + 4 * k + r]) * c->mats[16 * g + 4 * k + col];
+        dev = std::max(dev, std::abs(acc - (r == col ? 1.0 : 0.0)));
+      }
+    if (!(dev <= 1e-6)) {
+      delete c;
+      return fail(ctx, PC_ERR_NONUNITARY, "gate " + std::to_string(g) + " is not unitary");
+    }
+  }
+  c->oneq_q.assign(oneq_qubits, oneq_qubits + n_oneq);
+  c->oneq_m.resize(4 * n_oneq);
+  for (int64_t k = 0; k < n_oneq; ++k) {
+    if (oneq_qubits[k] < 0 || oneq_qubits[k] >= n_qubits) {
+      delete c;
+      return fail(ctx, PC_ERR_INVALID_ARG, "one-qubit gate on a bad qubit");
+    }
+    for (int e = 0; e < 4; ++e) c->oneq_m[4 * k + e] = cplx(oneq_mats[8 * k + 2 * e], oneq_mats[8 * k + 2 * e + 1]);
+  }
+  c->split = split_index;
+  std::vector<int> lorder, rorder;
+  for (int64_t g = split_index; g < n_gates; ++g) lorder.push_back((int)g);
+  for (int64_t g = split_index - 1; g >= 0; --g) rorder.push_back((int)g);
+  c->left_layers = make_layers(lorder, c->pairs.data(), n_qubits);
+  c->right_layers = make_layers(rorder, c->pairs.data(), n_qubits);
+  c->oneq_done = n_oneq == 0;
+  pc_status st = alloc_circuit(c);
+  if (st != PC_OK) { free_circuit(c); return st; }
+  st = reset_identity(c);
+  if (st != PC_OK) { free_circuit(c); return st; }
+  *out = c;
+  return PC_OK;
+}
+
+pc_status pc_destroy_circuit(pc_circuit* c) {
+  free_circuit(c);
+  return PC_OK;
+}
+
+pc_status pc_contract(pc_circuit* c, pc_stats* stats) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
+  const double t0 = now_s();
+  c->stats = pc_stats{};
+  const double tau = ctx->cfg.tau;
+  pc_status st = PC_OK;
+  while (layers_remain(c)) {
+    bool first = true;
+    while ((first || (double)mpo_size(c) < tau) && layers_remain(c)) {
+      st = absorb_layer_pair(c);
+      if (st != PC_OK) return st;
+      first = false;
+    }
+    int acc = 0;
+    st = unswap_stage(c, &acc);
+    if (st != PC_OK) return st;
+    if ((double)mpo_size(c) >= tau && layers_remain(c)) c->stats.stalled = 1;
+    c->stats.n_stages += 1;
+    c->stage += 1;
+  }
+  c->stats.final_size = mpo_size(c);
+  c->stats.max_chi = std::max(c->stats.max_chi, max_bond(c));
+  c->stats.seconds = now_s() - t0;
+  if (stats) *stats = c->stats;
+  return c->stats.stalled ? PC_WARN_STALLED : PC_OK;
+}
+
+pc_status pc_unswap(pc_circuit* c, int32_t* n_accepted) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  int acc = 0;
+  pc_status st = unswap_stage(c, &acc);
+  c->stage += 1;
+  if (n_accepted) *n_accepted = acc;
+  return st;
+}
+
+pc_status pc_get_bond_dims(pc_circuit* c, int32_t* chi) {
+  if (check_circuit(c) != PC_OK || !chi) return PC_ERR_INVALID_ARG;
+  for (int b = 0; b + 1 < c->n; ++b) chi[b] = c->chi[b + 1];
+  return PC_OK;
+}
+
+pc_status pc_get_layouts(pc_circuit* c, int32_t* layout_l, int32_t* layout_r) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  for (int q = 0; q < c->n; ++q) {
+    if (layout_l) layout_l[q] = c->lay[PC_SIDE_LEFT].pos[q];
+    if (layout_r) layout_r[q] = c->lay[PC_SIDE_RIGHT].pos[q];
+  }
+  return PC_OK;
+}
+
+pc_status pc_get_spectrum(pc_circuit* c, int32_t bond, int32_t cap, double* s, int32_t* len) {
+  if (check_circuit(c) != PC_OK || bond < 0 || bond + 1 >= c->n || !len) return PC_ERR_INVALID_ARG;
+  const int k = c->chi[bond + 1];
+  *len = k;
+  if (s && cap > 0) {
+    CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c->ctx, cudaMemcpy(s, lam_ptr(c, bond), std::min(k, cap) * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return PC_OK;
+}
+
+pc_status pc_get_site(pc_circuit* c, int32_t j, int64_t cap, double* out, int32_t* dims) {
+  if (check_circuit(c) != PC_OK || j < 0 || j >= c->n) return PC_ERR_INVALID_ARG;
+  const int64_t cnt = (int64_t)c->chi[j] * 4 * c->chi[j + 1];
+  if (dims) { dims[0] = c->chi[j]; dims[1] = c->chi[j + 1]; }
+  if (out) {
+    if (cap < cnt) return fail(c->ctx, PC_ERR_INVALID_ARG, "site buffer too small");
+    CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c->ctx, cudaMemcpy(out, site_ptr(c, j), cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+  }
+  return PC_OK;
+}
+
+pc_status pc_set_state(pc_circuit* c, const int32_t* chi, const double* sites, const double* lam) {
+  if (check_circuit(c) != PC_OK || !chi || !sites || !lam) return PC_ERR_INVALID_ARG;
+  if (chi[0] != 1 || chi[c->n] != 1) return fail(c->ctx, PC_ERR_INVALID_ARG, "boundary bond dimensions must be 1");
+  for (int k = 1; k < c->n; ++k)
+    if (chi[k] < 1 || chi[k] > c->chi_max) return fail(c->ctx, PC_ERR_INVALID_ARG, "bond dimension out of range");
+  size_t so = 0, lo = 0;
+  for (int j = 0; j < c->n; ++j) {
+    const size_t cnt = (size_t)chi[j] * 4 * chi[j + 1];
+    CUDA_TRY(c->ctx, cudaMemcpy(site_ptr(c, j), sites + 2 * so, cnt * sizeof(double2), cudaMemcpyHostToDevice));
+    so += cnt;
+  }
+  for (int b = 0; b + 1 < c->n; ++b) {
+    CUDA_TRY(c->ctx, cudaMemcpy(lam_ptr(c, b), lam + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice));
+    lo += chi[b + 1];
+  }
+  for (int k = 0; k <= c->n; ++k) c->chi[k] = chi[k];
+  c->lay[0].reset(c->n);
+  c->lay[1].reset(c->n);
+  c->projected = false;
+  return PC_OK;
+}
+
+pc_status pc_apply_updates(pc_circuit* c, int32_t n_ops, const int32_t* bonds, const double* ops, int32_t* chi_out) {
+  if (check_circuit(c) != PC_OK || n_ops < 0 || (n_ops > 0 && (!bonds || !ops))) return PC_ERR_INVALID_ARG;
+  if (n_ops > c->max_tasks) return fail(c->ctx, PC_ERR_INVALID_ARG, "more updates than the batch limit (n/2, at most 32)");
+  std::vector<int> sorted(bonds, bonds + n_ops);
+  std::sort(sorted.begin(), sorted.end());
+  for (int k = 0; k < n_ops; ++k) {
+    if (sorted[k] < 0 || sorted[k] + 1 >= c->n) return fail(c->ctx, PC_ERR_INVALID_ARG, "bond out of range");
+    if (k > 0 && sorted[k] - sorted[k - 1] < 2) return fail(c->ctx, PC_ERR_INVALID_ARG, "bonds must be non-adjacent");
+  }
+  std::vector<WaveItem> items(n_ops);
+  for (int k = 0; k < n_ops; ++k) {
+    items[k].bond = bonds[k];
+    for (int e = 0; e < 256; ++e) items[k].op[e] = cplx(ops[512 * k + 2 * e], ops[512 * k + 2 * e + 1]);
+  }
+  std::vector<int> counts;
+  pc_status st = run_wave(c, items, counts, nullptr, false, false, nullptr);
+  if (st != PC_OK) return st;
+  if (chi_out) for (int k = 0; k < n_ops; ++k) chi_out[k] = counts[k];
+  return PC_OK;
+}
+
+pc_status pc_plan_routing(int32_t n_qubits, int64_t n_gates, const int32_t* pairs, int64_t split_index, int64_t cap,
+                          int32_t* rec, int64_t* n_rec) {
+  if (n_qubits < 2 || n_gates < 0 || (n_gates > 0 && !pairs) || !n_rec) return PC_ERR_INVALID_ARG;
+  if (split_index < 0) split_index = n_gates / 2;
+  if (split_index > n_gates) return PC_ERR_INVALID_ARG;
+  for (int64_t g = 0; g < n_gates; ++g) {
+    const int a = pairs[2 * g], b = pairs[2 * g + 1];
+    if (a < 0 || b < 0 || a >= n_qubits || b >= n_qubits || a == b) return PC_ERR_INVALID_ARG;
+  }
+  std::vector<int> lorder, rorder;
+  for (int64_t g = split_index; g < n_gates; ++g) lorder.push_back((int)g);
+  for (int64_t g = split_index - 1; g >= 0; --g) rorder.push_back((int)g);
+  auto L = make_layers(lorder, pairs, n_qubits);
+  auto R = make_layers(rorder, pairs, n_qubits);
+  Layout lay[2];
+  lay[0].reset(n_qubits);
+  lay[1].reset(n_qubits);
+  int64_t k = 0;
+  auto emit = [&](const std::vector<ResolvedOp>& ops) {
+    for (const auto& op : ops) {
+      if (rec && k < cap) {
+        rec[4 * k + 0] = op.side; rec[4 * k + 1] = op.bond; rec[4 * k + 2] = op.kind; rec[4 * k + 3] = op.gate;
+      }
+      ++k;
+    }
+  };
+  const size_t nl = std::max(L.size(), R.size());
+  for (size_t i = 0; i < nl; ++i) {
+    if (i < L.size()) emit(plan_layer(PC_SIDE_LEFT, L[i], pairs, lay[0]));
+    if (i < R.size()) emit(plan_layer(PC_SIDE_RIGHT, R[i], pairs, lay[1]));
+  }
+  *n_rec = k;
+  return PC_OK;
+}
+
+pc_status pc_get_plan(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec) {
+  if (check_circuit(c) != PC_OK || !n_rec) return PC_ERR_INVALID_ARG;
+  *n_rec = (int64_t)c->plan_log.size();
+  for (int64_t k = 0; rec && k < cap && k < *n_rec; ++k)
+    for (int e = 0; e < 5; ++e) rec[5 * k + e] = c->plan_log[k][e];
+  return PC_OK;
+}
+
+pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec) {
+  if (check_circuit(c) != PC_OK || !n_rec) return PC_ERR_INVALID_ARG;
+  *n_rec = (int64_t)c->unswap_log.size();
+  for (int64_t k = 0; rec && k < cap && k < *n_rec; ++k)
+    for (int e = 0; e < 4; ++e) rec[4 * k + e] = c->unswap_log[k][e];
+  return PC_OK;
+}
+
+pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, double* p_peak, double* norm2) {
+  if (check_circuit(c) != PC_OK || !bits || !p_peak) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  pc_status st = project(c);
+  if (st != PC_OK) return st;
+  const int n = c->n;
+  const double Z = c->norm2;
+  if (!(Z > 0.0)) return fail(ctx, PC_ERR_STATE, "M|0> has zero norm");
+  if (max_expansions <= 0) max_expansions = 100000;
+  // Best-first search: pop the open prefix with the largest marginal (ties: lexicographic
+  // prefix, shorter first); the first complete string popped is the exact argmax.
+  struct Node {
+    double marg;
+    std::vector<uint8_t> prefix;
+    int64_t slot;
+  };
+  auto worse = [](const Node& a, const Node& b) {
+    if (a.marg != b.marg) return a.marg < b.marg;
+    return b.prefix < a.prefix;
+  };
+  std::priority_queue<Node, std::vector<Node>, decltype(worse)> heap(worse);
+  const int CH = c->chi_max;
+  int64_t cap_slots = 4096;
+  double2* pool = nullptr;
+  double* d_marg = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&pool, (size_t)cap_slots * CH * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&d_marg, 2 * sizeof(double)));
+  CUDA_TRY(ctx, pc::launch_fill_ones(pool, 1, c->stream));
+  int64_t used = 1;
+  heap.push(Node{1.0, {}, 0});
+  int64_t expansions = 0;
+  pc_status result = PC_ERR_NOT_PEAKED;
+  double hm[2];
+  while (!heap.empty()) {
+    Node top = heap.top();
+    heap.pop();
+    if ((int)top.prefix.size() == n) {
+      for (int q = 0; q < n; ++q) bits[q] = top.prefix[c->lay[PC_SIDE_LEFT].pos[q]];
+      *p_peak = top.marg;
+      if (norm2) *norm2 = Z * std::ldexp(1.0, n);
+      result = PC_OK;
+      break;
+    }
+    if (++expansions > max_expansions) break;
+    if (used + 2 > cap_slots) {
+      double2* bigger = nullptr;
+      cudaError_t e = cudaMalloc(&bigger, (size_t)cap_slots * 2 * CH * sizeof(double2));
+      if (e != cudaSuccess) { cudaFree(pool); cudaFree(d_marg); return fail(ctx, PC_ERR_OOM, "peak search pool"); }
+      cudaMemcpyAsync(bigger, pool, (size_t)used * CH * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream);
+      cudaStreamSynchronize(c->stream);
+      cudaFree(pool);
+      pool = bigger;
+      cap_slots *= 2;
+    }
+    const int j = (int)top.prefix.size();
+    const int cl = c->chi[j], cr = c->chi[j + 1];
+    double2* w0 = pool + (size_t)used * CH;
+    double2* w1 = pool + (size_t)(used + 1) * CH;
+    cudaError_t e = pc::launch_expand(pool + (size_t)top.slot * CH, site_ptr(c, j), cl, cr, c->d_env + c->env_off[j + 1],
+                                      w0, w1, d_marg, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm, d_marg, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(pool); cudaFree(d_marg); return fail(ctx, PC_ERR_CUDA, cudaGetErrorString(e)); }
+    for (int sg = 0; sg < 2; ++sg) {
+      Node ch{hm[sg] / Z, top.prefix, used + sg};
+      ch.prefix.push_back((uint8_t)sg);
+      heap.push(std::move(ch));
+    }
+    used += 2;
+  }
+  cudaFree(pool);
+  cudaFree(d_marg);
+  if (result != PC_OK) return fail(ctx, PC_ERR_NOT_PEAKED, "peak search exceeded the expansion cap");
+  return PC_OK;
+}
+
+namespace {
+
+// Shared driver of sampling and amplitudes: V (rows x chi_j) is pushed through each site.
+pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site_bits, bool sampling,
+                     double2* d_amp_out) {
+  pc_ctx* ctx = c->ctx;
+  const int n = c->n, CH = c->chi_max;
+  double2 *V = nullptr, *V2 = nullptr, *W0 = nullptr, *W1 = nullptr, *Y = nullptr;
+  double *m0 = nullptr, *m1 = nullptr;
+  const size_t sz = (size_t)rows * CH * sizeof(double2);
+  auto cleanup = [&]() { cudaFree(V); cudaFree(V2); cudaFree(W0); cudaFree(W1); cudaFree(Y); cudaFree(m0); cudaFree(m1); };
+  if (cudaMalloc(&V, sz) != cudaSuccess || cudaMalloc(&V2, sz) != cudaSuccess || cudaMalloc(&W0, sz) != cudaSuccess ||
+      cudaMalloc(&W1, sz) != cudaSuccess || cudaMalloc(&Y, sz) != cudaSuccess ||
+      cudaMalloc(&m0, rows * sizeof(double)) != cudaSuccess || cudaMalloc(&m1, rows * sizeof(double)) != cudaSuccess) {
+    cleanup();
+    return fail(ctx, PC_ERR_OOM, "sampling buffers");
+  }
+  cudaError_t e = pc::launch_fill_ones(V, rows, c->stream);
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const int cl = c->chi[j], cr = c->chi[j + 1];
+    pc::GemmDesc g[2];
+    for (int sg = 0; sg < 2; ++sg) {
+      g[sg] = pc::GemmDesc{};
+      g[sg].A = V; g[sg].lda = cl;
+      g[sg].B = site_ptr(c, j) + 2 * sg * cr; g[sg].ldb = 4 * cr;
+      g[sg].C = sg ? W1 : W0; g[sg].ldc = cr;
+      g[sg].M = rows; g[sg].N = cr; g[sg].K = cl; g[sg].opB = 0; g[sg].alpha = 1.0;
+    }
+    c->h_gemm[0] = g[0];
+    c->h_gemm[1] = g[1];
+    e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, 2 * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 2, rows, cr, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) break;
+    if (sampling) {
+      for (int sg = 0; sg < 2 && e == cudaSuccess; ++sg) {
+        pc::GemmDesc q{};
+        q.A = sg ? W1 : W0; q.lda = cr;
+        q.B = c->d_env + c->env_off[j + 1]; q.ldb = cr;
+        q.C = Y; q.ldc = cr;
+        q.M = rows; q.N = cr; q.K = cr; q.opB = 0; q.alpha = 1.0;
+        c->h_gemm[0] = q;
+        e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 1, rows, cr, c->stream);
+        if (e == cudaSuccess) e = pc::launch_quadform_rows(q.A, Y, rows, cr, cr, sg ? m1 : m0, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      }
+      if (e == cudaSuccess) e = pc::launch_sample_pick(W0, W1, m0, m1, d_u, rows, cr, j, n, V2, d_site_bits, c->stream);
+    } else {
+      e = pc::launch_amp_pick(W0, W1, d_site_bits, rows, cr, j, n, V2, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    std::swap(V, V2);
+  }
+  pc_status st = PC_OK;
+  if (e != cudaSuccess) st = fail(ctx, PC_ERR_CUDA, cudaGetErrorString(e));
+  // amplitudes: the final V is rows x 1 (chi_n = 1)
+  if (st == PC_OK && !sampling) e = cudaMemcpy(d_amp_out, V, rows * sizeof(double2), cudaMemcpyDeviceToDevice);
+  cleanup();
+  if (e != cudaSuccess && st == PC_OK) st = fail(ctx, PC_ERR_CUDA, cudaGetErrorString(e));
+  return st;
+}
+
+}  // namespace
+
+pc_status pc_sample(pc_circuit* c, int64_t n_samples, uint64_t seed, uint8_t* bits) {
+  if (check_circuit(c) != PC_OK || n_samples < 0 || (n_samples > 0 && !bits)) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  pc_status st = project(c);
+  if (st != PC_OK) return st;
+  const int n = c->n;
+  const int64_t chunk = 4096;
+  std::vector<double> u;
+  std::vector<uint8_t> sb;
+  for (int64_t base = 0; base < n_samples; base += chunk) {
+    const int rows = (int)std::min(chunk, n_samples - base);
+    u.resize((size_t)rows * n);
+    for (int s = 0; s < rows; ++s)
+      for (int j = 0; j < n; ++j)
+        u[(size_t)s * n + j] = (double)(splitmix64(seed, (uint64_t)(base + s) * n + j) >> 11) * (1.0 / 9007199254740992.0);
+    double* d_u = nullptr;
+    uint8_t* d_sb = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&d_u, u.size() * sizeof(double)));
+    if (cudaMalloc(&d_sb, (size_t)rows * n) != cudaSuccess) { cudaFree(d_u); return fail(ctx, PC_ERR_OOM, "sample bits"); }
+    cudaMemcpy(d_u, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice);
+    st = sweep_rows(c, rows, d_u, d_sb, true, nullptr);
+    sb.resize((size_t)rows * n);
+    if (st == PC_OK) cudaMemcpy(sb.data(), d_sb, sb.size(), cudaMemcpyDeviceToHost);
+    cudaFree(d_u);
+    cudaFree(d_sb);
+    if (st != PC_OK) return st;
+    for (int s = 0; s < rows; ++s)
+      for (int q = 0; q < n; ++q) bits[(size_t)(base + s) * n + q] = sb[(size_t)s * n + c->lay[PC_SIDE_LEFT].pos[q]];
+  }
+  return PC_OK;
+}
+
+pc_status pc_amplitudes(pc_circuit* c, int64_t k, const uint8_t* bits, double* amp) {
+  if (check_circuit(c) != PC_OK || k < 0 || (k > 0 && (!bits || !amp))) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  pc_status st = project(c);
+  if (st != PC_OK) return st;
+  const int n = c->n;
+  const int64_t chunk = 4096;
+  const double scale = std::pow(2.0, n / 2.0);
+  std::vector<uint8_t> sb;
+  std::vector<double2> res;
+  for (int64_t base = 0; base < k; base += chunk) {
+    const int rows = (int)std::min(chunk, k - base);
+    sb.resize((size_t)rows * n);
+    for (int s = 0; s < rows; ++s)
+      for (int q = 0; q < n; ++q) sb[(size_t)s * n + c->lay[PC_SIDE_LEFT].pos[q]] = bits[(size_t)(base + s) * n + q];
+    uint8_t* d_sb = nullptr;
+    double2* d_amp = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&d_sb, sb.size()));
+    if (cudaMalloc(&d_amp, rows * sizeof(double2)) != cudaSuccess) { cudaFree(d_sb); return fail(ctx, PC_ERR_OOM, "amplitudes"); }
+    cudaMemcpy(d_sb, sb.data(), sb.size(), cudaMemcpyHostToDevice);
+    st = sweep_rows(c, rows, nullptr, d_sb, false, d_amp);
+    res.resize(rows);
+    if (st == PC_OK && cudaMemcpy(res.data(), d_amp, rows * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = fail(ctx, PC_ERR_CUDA, "amplitude copy");
+    cudaFree(d_sb);
+    cudaFree(d_amp);
+    if (st != PC_OK) return st;
+    for (int s = 0; s < rows; ++s) {
+      amp[2 * (base + s)] = res[s].x * scale;
+      amp[2 * (base + s) + 1] = res[s].y * scale;
+    }
+  }
+  return PC_OK;
+}
+
+pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  for (int k = 0; k < 5; ++k) {
+    if (launches) launches[k] = c->t_launch[k];
+    if (ms) ms[k] = c->t_ms[k];
+  }
+  return PC_OK;
+}
+
+pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  for (int k = 0; k < 5; ++k) { c->t_launch[k] = 0; c->t_ms[k] = 0.0; }
+  c->timing = enable != 0;
+  return PC_OK;
+}
+
+}  // extern "C"

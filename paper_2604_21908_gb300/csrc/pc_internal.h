@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's host code (pc_api.cpp) and its kernels
+// (kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pc {
+
+// One complex FP64 GEMM of a batch: C = alpha * A * op(B) (+ C if accumulate).
+//   A  : M x K row-major, leading dimension lda (complex elements)
+//   B  : op == 0: K x N row-major (ldb);  op == 1: N x K row-major (ldb), used as its
+//        conjugate transpose
+//   C  : M x N row-major (ldc)
+// Optional row scaling of A by a real vector (row_scale[i] multiplies row i of A).
+struct GemmDesc {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  const double* row_scale;
+  int32_t M, N, K;
+  int32_t lda, ldb, ldc;
+  int32_t opB;          // 0: B, 1: B^H
+  int32_t accumulate;   // 0: C = ..., 1: C += ...
+  double alpha;
+};
+
+// One two-site update of a wave (Sec. II.B.1): sites (j, j+1) with bond dims
+// chi_l = chi_{j-1}, chi_m = chi_j, chi_r = chi_{j+1}.
+struct UpdateTask {
+  const double2* Bl;      // B_j  [chi_l][4][chi_m]
+  const double2* Br;      // B_j+1 [chi_m][4][chi_r]
+  const double* lam_l;    // lambda_{j-1} [chi_l], nullptr for the left boundary (1)
+  const double2* op;      // 16x16 operator on (p_j, p_j+1), row-major
+  double2* X;             // Jacobi input: the merged, gated, lambda-scaled bond matrix,
+                          // m x n row-major, or its transpose (n x m) when transposed
+  double2* T0;            // m x n: merged and gated, without lambda
+  int32_t chi_l, chi_m, chi_r;
+  int32_t m, n;           // 4*chi_l, 4*chi_r
+  int32_t transposed;     // 1 when m > n: the Jacobi orthogonalises the n columns
+};
+
+// Per-factorisation state of the batched one-sided Jacobi kernel.  The kernel makes the
+// m rows of X (each of length n) mutually orthogonal; m <= n always (the host transposes a
+// tall bond matrix), because more vectors than dimensions cannot all be made orthogonal.
+// When Q is given (m x m, set to the identity), every rotation is also applied to the rows
+// of Q, which then holds the accumulated unitary.
+struct JacobiTask {
+  double2* X;             // m x n row-major; rows are orthogonalised in place
+  double2* Q;             // optional m x m accumulator (nullptr: none)
+  int32_t m, n;
+  int32_t mp;             // m rounded up to even
+  int32_t pad_;
+};
+struct JacobiStatus {
+  unsigned int rot[3];    // rotations per sweep (ring of three)
+  int32_t sweeps;         // sweeps completed when the task stopped
+  int32_t converged;      // 1 converged, 0 hit the sweep cap
+  int32_t pad_[3];
+};
+
+// Result of truncation (Sec. II.B.1 cutoff, App. A.4 chi_max): count kept rows, their row
+// indices into X in descending order of norm, the kept normalised values and the norm.
+struct TruncOut {
+  int32_t count;
+  int32_t m;              // rows examined
+  double s0;              // largest singular value
+  double nrm;             // sqrt(sum of kept s^2)
+  double s_first_dropped; // first singular value not kept (0 if none)
+};
+
+// Launch wrappers (all asynchronous on `stream`; return cudaError_t of the launch).
+cudaError_t launch_gemm(const GemmDesc* d_desc, int batch, int max_m, int max_n, cudaStream_t stream);
+cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi_l, int max_chi_r,
+                              cudaStream_t stream);
+// Sets every task's accumulator Q (if any) to the identity.
+cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
+// Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the
+// caller), err = 1 int (zeroed): set to 1 if a grid barrier wait exceeded its limit.
+cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status,
+                          int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count,
+                          cudaStream_t stream);
+cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max,
+                            int32_t* d_idx, int idx_stride, double* d_lam, double* d_sraw,
+                            int lam_stride, TruncOut* d_out, cudaStream_t stream);
+// B_{j+1}'[k][c] = X[idx[k]][c] / s_idx[k] (rows path) or conj(Q[idx[k]][c]) (transposed
+// path: the accumulated right singular vectors) for each task; dst pointers per task.
+struct SplitRowsDesc {
+  const double2* X;
+  const double2* Q;       // non-null selects the transposed path
+  double2* dst;
+  const int32_t* idx;
+  const double* sraw;     // kept singular values (row norms), unnormalised
+  int32_t count, n;
+};
+cudaError_t launch_split_rows(const SplitRowsDesc* d_desc, int ntasks, int max_count, int max_n,
+                              cudaStream_t stream);
+cudaError_t launch_one_site(double2* B, int chi_l, int chi_r, const double2* g2_dev, int side,
+                            cudaStream_t stream);
+// Peak search: children of a prefix vector v (length chi_l) through site tensor B_j:
+// w_sigma = v A^sigma (A^sigma = B_j[:, 2 sigma, :]), m_sigma = w E w^H.
+cudaError_t launch_expand(const double2* v, const double2* Bj, int chi_l, int chi_r,
+                          const double2* E, double2* w0, double2* w1, double* marg,
+                          cudaStream_t stream);
+// Sampling/amplitude helpers.
+cudaError_t launch_quadform_rows(const double2* W, const double2* Y, int rows, int cols, int ld,
+                                 double* out, cudaStream_t stream);
+cudaError_t launch_sample_pick(const double2* W0, const double2* W1, const double* m0,
+                               const double* m1, const double* u, int S, int chi, int site,
+                               int n_sites, double2* Vnext, uint8_t* site_bits,
+                               cudaStream_t stream);
+cudaError_t launch_amp_pick(const double2* W0, const double2* W1, const uint8_t* site_bits, int K,
+                            int chi, int site, int n_sites, double2* Vnext, cudaStream_t stream);
+cudaError_t launch_fill_ones(double2* v, int rows, cudaStream_t stream);
+
+}  // namespace pc
