@@ -63,7 +63,7 @@ typedef struct pc_circuit pc_circuit;
 /* Hyperparameters of App. A.4 plus the library's own settings. */
 typedef struct pc_config {
   double eps;                /* SVD cutoff: keep s_k > eps * s_0 (relative, strict)       */
-  int32_t chi_max;           /* hard cap on every bond dimension, 1..4096                 */
+  int32_t chi_max;           /* hard cap on every bond dimension, 1..1024                 */
   double tau;                /* size(M) threshold (total tensor elements) for unswapping  */
   int32_t max_unswap_iter;   /* cap on unswap cycles per stage (paper: 20)                */
   int32_t accept_equal;      /* 0 strict (paper default), 1 also accept equal dimension   */
@@ -114,6 +114,23 @@ pc_status pc_destroy_circuit(pc_circuit* c);
  * Returns PC_WARN_STALLED (> 0) when the progress rule had to force absorption.
  * stats may be NULL. */
 pc_status pc_contract(pc_circuit* c, pc_stats* stats);
+
+/* At most max_iterations outer iterations of Algorithm 1 (each: absorb layer pairs while
+ * size(M) < tau, at least one pair; then one unswap stage).  Returns PC_OK while layers
+ * remain as well as when done; *done (may be NULL) is set to 1 once every layer is absorbed.
+ * stats (may be NULL) receives the counters of this call only. */
+pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats* stats, int32_t* done);
+
+/* Layer cursors of the two fronts (number of layers of C_L / C_R already absorbed). */
+pc_status pc_get_cursors(pc_circuit* c, int64_t* left, int64_t* right);
+pc_status pc_set_cursors(pc_circuit* c, int64_t left, int64_t right);
+
+/* Device-side checkpoint of the contraction state: the MPO (sites, spectra, bond
+ * dimensions), both layouts and both cursors.  pc_snapshot copies the state into a buffer
+ * owned by the circuit (allocated on first use); pc_restore copies it back.  Both are
+ * device-to-device copies on the circuit's stream. */
+pc_status pc_snapshot(pc_circuit* c);
+pc_status pc_restore(pc_circuit* c);
 
 /* One unswap stage (Sec. II.B.2) on the current MPO, in the configured mode.
  * *n_accepted (may be NULL) receives the number of accepted swaps. */
@@ -171,11 +188,21 @@ pc_status pc_plan_routing(int32_t n_qubits, int64_t n_gates, const int32_t* pair
 pc_status pc_get_plan(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec);
 pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n_rec);
 
-/* Timing of the dominant kernels since the last pc_reset_kernel_timers, measured with CUDA
- * events on the circuit's stream: per kernel class (0 merge, 1 jacobi, 2 truncate, 3 split,
- * 4 other) the launch count and total milliseconds; arrays of length 5. */
-pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms);
+/* Kernel accounting since the last pc_reset_kernel_timers.  Per kernel class (0 merge and
+ * gate, 1 Jacobi factorisation, 2 truncation, 3 split, 4 everything else: environments,
+ * peak search, sampling, one-qubit gates, accumulator set-up) the number of kernel launches
+ * and, when timing is enabled, the total milliseconds measured with CUDA events on the
+ * circuit's stream (class 4 is counted, not timed) and the algorithmic floating-point work:
+ * class 0: 8 * 4chi_l * chi_m * 4chi_r + 8 * 256 * chi_l * chi_r (complex merge + gate);
+ * class 1: 4 * (4 M^2 N + 22 N^3) with M >= N the bond matrix sides (textbook thin SVD
+ * with both singular-vector sets, complex); class 3: 8 * m * n * k (B_j = T0 V).
+ * launches, ms, flops: arrays of length 5 (any may be NULL). */
+pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops);
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
+
+/* The CUDA stream (a cudaStream_t) every kernel of this circuit runs on, for callers that
+ * time or order their own work against it.  The circuit keeps ownership. */
+pc_status pc_get_stream(pc_circuit* c, void** stream);
 
 /* Library version string. */
 const char* pc_version(void);

@@ -49,7 +49,8 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_destroy_circuit", "pc_contract", "pc_unswap", "pc_extract_peak", "pc_sample", "pc_amplitudes",
            "pc_get_bond_dims", "pc_get_layouts", "pc_get_spectrum", "pc_get_site", "pc_set_state",
            "pc_apply_updates", "pc_plan_routing", "pc_get_plan", "pc_get_unswap_log", "pc_kernel_timers",
-           "pc_reset_kernel_timers"]
+           "pc_reset_kernel_timers", "pc_contract_iterations", "pc_get_cursors", "pc_set_cursors", "pc_snapshot",
+           "pc_restore", "pc_get_stream"]
 
 
 def _p(t):
@@ -89,7 +90,13 @@ def load(path: str = LIB_PATH):
         "pc_plan_routing": ([i32, i64, vp, i64, i64, vp, _p(i64)], i32),
         "pc_get_plan": ([vp, i64, vp, _p(i64)], i32),
         "pc_get_unswap_log": ([vp, i64, vp, _p(i64)], i32),
-        "pc_kernel_timers": ([vp, vp, vp], i32),
+        "pc_kernel_timers": ([vp, vp, vp, vp], i32),
+        "pc_contract_iterations": ([vp, i32, _p(PcStats), _p(i32)], i32),
+        "pc_get_cursors": ([vp, _p(i64), _p(i64)], i32),
+        "pc_set_cursors": ([vp, i64, i64], i32),
+        "pc_snapshot": ([vp], i32),
+        "pc_restore": ([vp], i32),
+        "pc_get_stream": ([vp, _p(vp)], i32),
         "pc_reset_kernel_timers": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -199,6 +206,35 @@ class Circuit:
         d["status"] = st
         return d
 
+    def contract_iterations(self, max_iterations: int):
+        stats = PcStats()
+        done = C.c_int32(0)
+        self._chk(self.lib.pc_contract_iterations(self.h, max_iterations, C.byref(stats), C.byref(done)),
+                  "pc_contract_iterations")
+        d = stats.as_dict()
+        d["done"] = bool(done.value)
+        return d
+
+    def cursors(self):
+        a, b = C.c_int64(0), C.c_int64(0)
+        self._chk(self.lib.pc_get_cursors(self.h, C.byref(a), C.byref(b)), "pc_get_cursors")
+        return a.value, b.value
+
+    def set_cursors(self, left: int, right: int):
+        self._chk(self.lib.pc_set_cursors(self.h, left, right), "pc_set_cursors")
+
+    def stream_handle(self) -> int:
+        """The circuit's cudaStream_t as an integer (for torch.cuda.ExternalStream)."""
+        h = C.c_void_p()
+        self._chk(self.lib.pc_get_stream(self.h, C.byref(h)), "pc_get_stream")
+        return h.value or 0
+
+    def snapshot(self):
+        self._chk(self.lib.pc_snapshot(self.h), "pc_snapshot")
+
+    def restore(self):
+        self._chk(self.lib.pc_restore(self.h), "pc_restore")
+
     def unswap(self) -> int:
         acc = C.c_int32(0)
         self._chk(self.lib.pc_unswap(self.h, C.byref(acc)), "pc_unswap")
@@ -280,10 +316,12 @@ class Circuit:
         self._chk(self.lib.pc_reset_kernel_timers(self.h, 1 if enable else 0), "pc_reset_kernel_timers")
 
     def timers(self):
+        """(launches, ms, flops) per kernel class: merge+gate, Jacobi, truncate, split, other."""
         la = np.zeros(5, dtype=np.int64)
         ms = np.zeros(5)
-        self._chk(self.lib.pc_kernel_timers(self.h, _ptr(la), _ptr(ms)), "pc_kernel_timers")
-        return la, ms
+        fl = np.zeros(5)
+        self._chk(self.lib.pc_kernel_timers(self.h, _ptr(la), _ptr(ms), _ptr(fl)), "pc_kernel_timers")
+        return la, ms, fl
 
     def close(self):
         if self.h:

@@ -175,20 +175,59 @@ __device__ bool grid_barrier(unsigned int* bar, int* err, unsigned int nblocks) 
 }
 
 constexpr int JAC_MAX_TASKS = 256;
-constexpr int JAC_THREADS = 256;
+constexpr int JAC_THREADS = 512;
+constexpr int JAC_E = 8;            // row elements per thread held in registers
+
+// Rotates one pair of rows of length len held by a group of GT threads: either in registers
+// (len <= GT * JAC_E) or streamed from memory.
+struct Rot {
+  double c, sn, wx, wy, zx, zy;
+};
+
+__device__ __forceinline__ void rot_apply(const Rot& q, double2& u, double2& v) {
+  double2 na, nb;
+  na.x = q.c * u.x - (q.wx * v.x - q.wy * v.y);
+  na.y = q.c * u.y - (q.wx * v.y + q.wy * v.x);
+  nb.x = q.sn * u.x + (q.zx * v.x - q.zy * v.y);
+  nb.y = q.sn * u.y + (q.zx * v.y + q.zy * v.x);
+  u = na;
+  v = nb;
+}
+
+// Sum of four values over the GT threads of a group, identical on every thread.
+template <int G>
+__device__ __forceinline__ void group_sum4(double& a, double& b, double& c, double& d, double (*red)[4],
+                                           int grp, int gl) {
+  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c); d = warp_sum(d);
+  if constexpr (G > 1) {
+    const int w = gl >> 5;
+    if ((gl & 31) == 0) { red[w][0] = a; red[w][1] = b; red[w][2] = c; red[w][3] = d; }
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
+    a = b = c = d = 0.0;
+#pragma unroll
+    for (int k = 0; k < G; ++k) { a += red[k][0]; b += red[k][1]; c += red[k][2]; d += red[k][3]; }
+  }
+}
 
 // One-sided (Hestenes) Jacobi on the rows of each task's matrix: rotate pairs of rows until
 // every pair is orthogonal to |<x_a, x_b>| <= tol |x_a| |x_b|, tol = 2 eps_64 sqrt(n).
 // Pairs follow the round-robin (circle) ordering: in round r of a sweep over mp rows,
 // pair 0 = (mp-1, r), pair i = ((r+i) mod (mp-1), (r-i) mod (mp-1)).  Each global iteration
 // runs one round of every unfinished task (tasks of different sizes advance their own
-// sweeps), then all CTAs meet at a grid barrier.  One warp rotates one pair.
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacobiTask* __restrict__ tasks,
-                                                            int ntasks, JacobiStatus* st,
-                                                            int max_sweeps, unsigned int* bar,
-                                                            int* err) {
+// sweeps), then all CTAs meet at a grid barrier.  A group of G warps rotates one pair.
+// Squared row norms are computed exactly in round 0 of every sweep and carried through the
+// sweep with the exact-arithmetic update a' = a - t|g|, b' = b + t|g|; a sweep with no
+// rotation leaves them untouched, so the convergence decision always uses exact norms.
+template <int G>
+__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask* __restrict__ tasks,
+                                                               int ntasks, JacobiStatus* st,
+                                                               int max_sweeps, unsigned int* bar,
+                                                               int* err) {
+  constexpr int GT = 32 * G;
+  constexpr int NG = JAC_THREADS / GT;
   __shared__ int s_off[JAC_MAX_TASKS + 1];
   __shared__ unsigned char s_done[JAC_MAX_TASKS];
+  __shared__ double s_red[2][NG][G][4];
   if (threadIdx.x == 0) {
     int off = 0;
     for (int t = 0; t < ntasks; ++t) { s_off[t] = off; off += tasks[t].mp >> 1; }
@@ -196,15 +235,13 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacobiTask* _
   }
   for (int t = threadIdx.x; t < ntasks; t += blockDim.x) s_done[t] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int gwarp = blockIdx.x * (JAC_THREADS / 32) + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * (JAC_THREADS / 32);
+  const int grp = threadIdx.x / GT, gl = threadIdx.x % GT;
+  const int ggrp = blockIdx.x * NG + grp, ngrp = gridDim.x * NG;
   const int total = s_off[ntasks];
   const double eps64 = 2.220446049250313e-16;
+  int parity = 0;
 
   for (long long g = 0;; ++g) {
-    // Per-task bookkeeping, computed identically by every CTA from global counters that
-    // were final at the last barrier.
     for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
       if (s_done[t]) continue;
       const long long R = tasks[t].mp - 1;
@@ -225,7 +262,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacobiTask* _
     for (int t = threadIdx.x; t < ntasks; t += blockDim.x) mine &= s_done[t];
     if (__syncthreads_and(mine)) break;
 
-    for (int item = gwarp; item < total; item += nwarps) {
+    for (int item = ggrp; item < total; item += ngrp) {
       int lo = 0, hi = ntasks - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -241,59 +278,112 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacobiTask* _
       int a, b;
       if (i == 0) { a = tk.mp - 1; b = r; }
       else { a = (r + i) % R; b = (r - i + R) % R; }
-      if (a >= tk.m || b >= tk.m) continue;
+      const bool full = (r == 0);
+      double (*red)[4] = s_red[parity][grp];
+      if (a >= tk.m || b >= tk.m) {
+        // the padding row: in round 0 the real row still gets its exact norm
+        if (full) {
+          const int v = a < tk.m ? a : b;
+          const double2* xv = tk.X + (size_t)v * tk.n;
+          double acc = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+          for (int k = gl; k < tk.n; k += GT) acc = fma(xv[k].x, xv[k].x, fma(xv[k].y, xv[k].y, acc));
+          group_sum4<G>(acc, z1, z2, z3, red, grp, gl);
+          if (gl == 0) tk.nrm2[v] = acc;
+          parity ^= 1;
+        }
+        continue;
+      }
       double2* xa = tk.X + (size_t)a * tk.n;
       double2* xb = tk.X + (size_t)b * tk.n;
+      const int n = tk.n;
+      const bool in_regs = n <= GT * JAC_E;
+      double2 ra[JAC_E], rb[JAC_E];
       double aa = 0.0, bb = 0.0, gr = 0.0, gi = 0.0;
-      for (int k = lane; k < tk.n; k += 32) {
-        const double2 u = xa[k], v = xb[k];
-        aa = fma(u.x, u.x, fma(u.y, u.y, aa));
-        bb = fma(v.x, v.x, fma(v.y, v.y, bb));
-        gr = fma(u.x, v.x, fma(u.y, v.y, gr));
-        gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+      if (in_regs) {
+#pragma unroll
+        for (int e = 0; e < JAC_E; ++e) {
+          const int k = gl + e * GT;
+          ra[e] = k < n ? xa[k] : make_double2(0.0, 0.0);
+          rb[e] = k < n ? xb[k] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int e = 0; e < JAC_E; ++e) {
+          const double2 u = ra[e], v = rb[e];
+          gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+          gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+          if (full) {
+            aa = fma(u.x, u.x, fma(u.y, u.y, aa));
+            bb = fma(v.x, v.x, fma(v.y, v.y, bb));
+          }
+        }
+      } else {
+        for (int k = gl; k < n; k += GT) {
+          const double2 u = xa[k], v = xb[k];
+          gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+          gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+          if (full) {
+            aa = fma(u.x, u.x, fma(u.y, u.y, aa));
+            bb = fma(v.x, v.x, fma(v.y, v.y, bb));
+          }
+        }
       }
-      aa = warp_sum(aa); bb = warp_sum(bb); gr = warp_sum(gr); gi = warp_sum(gi);
+      group_sum4<G>(aa, bb, gr, gi, red, grp, gl);
+      parity ^= 1;
+      if (!full) { aa = tk.nrm2[a]; bb = tk.nrm2[b]; }
       // rows at the underflow floor are zero for every purpose here
-      if (aa < 1e-280 || bb < 1e-280) continue;
+      bool rotate = !(aa < 1e-280 || bb < 1e-280);
       const double gabs = hypot(gr, gi);
-      const double tol = 2.0 * eps64 * sqrt((double)tk.n);
-      if (!(gabs > tol * sqrt(aa) * sqrt(bb))) continue;
+      const double tol = 2.0 * eps64 * sqrt((double)n);
+      rotate = rotate && (gabs > tol * sqrt(aa) * sqrt(bb));
+      if (!rotate) {
+        if (full && gl == 0) { tk.nrm2[a] = aa; tk.nrm2[b] = bb; }
+        continue;
+      }
       // Real rotation on the phase-adjusted pair: zeta = (b - a) / (2|g|),
       // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t.
       const double zeta = (bb - aa) / (2.0 * gabs);
       double tt;
       if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
       else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      const double c = 1.0 / sqrt(1.0 + tt * tt);
-      const double sn = c * tt;
+      Rot q;
+      q.c = 1.0 / sqrt(1.0 + tt * tt);
+      q.sn = q.c * tt;
       const double ex = gr / gabs, ey = -gi / gabs;        // e^{-i phi}
-      const double wx = sn * ex, wy = sn * ey;             // s e^{-i phi}
-      const double zx = c * ex, zy = c * ey;               // c e^{-i phi}
-      for (int k = lane; k < tk.n; k += 32) {
-        const double2 u = xa[k], v = xb[k];
-        double2 na, nb;
-        na.x = c * u.x - (wx * v.x - wy * v.y);
-        na.y = c * u.y - (wx * v.y + wy * v.x);
-        nb.x = sn * u.x + (zx * v.x - zy * v.y);
-        nb.y = sn * u.y + (zx * v.y + zy * v.x);
-        xa[k] = na;
-        xb[k] = nb;
+      q.wx = q.sn * ex; q.wy = q.sn * ey;                  // s e^{-i phi}
+      q.zx = q.c * ex; q.zy = q.c * ey;                    // c e^{-i phi}
+      if (in_regs) {
+#pragma unroll
+        for (int e = 0; e < JAC_E; ++e) {
+          const int k = gl + e * GT;
+          if (k < n) {
+            rot_apply(q, ra[e], rb[e]);
+            xa[k] = ra[e];
+            xb[k] = rb[e];
+          }
+        }
+      } else {
+        for (int k = gl; k < n; k += GT) {
+          double2 u = xa[k], v = xb[k];
+          rot_apply(q, u, v);
+          xa[k] = u;
+          xb[k] = v;
+        }
       }
       if (tk.Q) {
         double2* qa = tk.Q + (size_t)a * tk.m;
         double2* qb = tk.Q + (size_t)b * tk.m;
-        for (int k = lane; k < tk.m; k += 32) {
-          const double2 u = qa[k], v = qb[k];
-          double2 na, nb;
-          na.x = c * u.x - (wx * v.x - wy * v.y);
-          na.y = c * u.y - (wx * v.y + wy * v.x);
-          nb.x = sn * u.x + (zx * v.x - zy * v.y);
-          nb.y = sn * u.y + (zx * v.y + zy * v.x);
-          qa[k] = na;
-          qb[k] = nb;
+        for (int k = gl; k < tk.m; k += GT) {
+          double2 u = qa[k], v = qb[k];
+          rot_apply(q, u, v);
+          qa[k] = u;
+          qb[k] = v;
         }
       }
-      if (lane == 0) atomicAdd(&st[t].rot[s % 3], 1u);
+      if (gl == 0) {
+        tk.nrm2[a] = aa - tt * gabs;
+        tk.nrm2[b] = bb + tt * gabs;
+        atomicAdd(&st[t].rot[s % 3], 1u);
+      }
     }
     if (!grid_barrier(bar, err, gridDim.x)) return;
   }
@@ -544,21 +634,30 @@ cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
-                          unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
-  if (ntasks <= 0) return cudaSuccess;
-  if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
+template <int G>
+cudaError_t launch_jacobi_g(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                            unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel, JAC_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel<G>, JAC_THREADS, 0);
     if (e != cudaSuccess) return e;
-    if (blocks_per_sm > 4) blocks_per_sm = 4;
+    if (blocks_per_sm > 1) blocks_per_sm = 1;
     if (blocks_per_sm < 1) return cudaErrorLaunchOutOfResources;
   }
-  int grid = sm_count * blocks_per_sm;
+  const int grid = sm_count * blocks_per_sm;
   void* args[] = {(void*)&d_tasks, (void*)&ntasks, (void*)&d_status, (void*)&max_sweeps, (void*)&d_bar,
                   (void*)&d_err};
-  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<G>, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+}
+
+cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                          unsigned int* d_bar, int* d_err, int sm_count, int max_len, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
+  // group width: enough threads to hold the longest row in registers, at most 4 warps
+  if (max_len <= 32 * JAC_E) return launch_jacobi_g<1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  if (max_len <= 64 * JAC_E) return launch_jacobi_g<2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  return launch_jacobi_g<4>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
 }
 
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max, int32_t* d_idx,

@@ -151,6 +151,7 @@ struct pc_circuit {
   double2* d_X = nullptr;
   double2* d_T0 = nullptr;
   double2* d_Q = nullptr;         // Jacobi accumulators (transposed path)
+  double* d_nrm = nullptr;        // Jacobi squared row norms
   size_t scratch_elems = 0;       // per task
   double2* d_ops = nullptr;
   pc::UpdateTask* d_tasks = nullptr;
@@ -191,6 +192,15 @@ struct pc_circuit {
   cudaEvent_t ev[6] = {};
   int64_t t_launch[5] = {};
   double t_ms[5] = {};
+  double t_flops[5] = {};
+  // device-side checkpoint
+  double2* d_snap_sites = nullptr;
+  double* d_snap_lam = nullptr;
+  bool has_snapshot = false;
+  std::vector<int> snap_chi;
+  Layout snap_lay[2];
+  size_t snap_lcur = 0, snap_rcur = 0;
+  bool snap_oneq_done = true;
 };
 
 namespace {
@@ -225,11 +235,13 @@ int max_bond(const pc_circuit* c) {
 
 void free_circuit(pc_circuit* c) {
   if (!c) return;
-  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_ops);
+  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_nrm); cudaFree(c->d_ops);
   cudaFree(c->d_tasks); cudaFree(c->d_jtasks); cudaFree(c->d_gemm); cudaFree(c->d_gemm2);
   cudaFree(c->d_split); cudaFree(c->d_jst); cudaFree(c->d_tout); cudaFree(c->d_idx);
   cudaFree(c->d_lamnew); cudaFree(c->d_sraw); cudaFree(c->d_bar); cudaFree(c->d_err); cudaFree(c->d_g2);
   cudaFree(c->d_env);
+  cudaFree(c->d_snap_sites);
+  cudaFree(c->d_snap_lam);
   cudaFreeHost(c->h_ops); cudaFreeHost(c->h_tasks); cudaFreeHost(c->h_jtasks); cudaFreeHost(c->h_gemm);
   cudaFreeHost(c->h_gemm2); cudaFreeHost(c->h_split); cudaFreeHost(c->h_jst); cudaFreeHost(c->h_tout);
   cudaFreeHost(c->h_err);
@@ -259,6 +271,7 @@ pc_status alloc_circuit(pc_circuit* c) {
   CUDA_TRY(ctx, cudaMalloc(&c->d_X, (size_t)T * c->scratch_elems * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_T0, (size_t)T * c->scratch_elems * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_Q, (size_t)T * c->scratch_elems * sizeof(double2)));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_nrm, (size_t)T * 4 * X * sizeof(double)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_ops, (size_t)T * 256 * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_tasks, T * sizeof(pc::UpdateTask)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_jtasks, T * sizeof(pc::JacobiTask)));
@@ -313,6 +326,9 @@ void timer_mark(pc_circuit* c, int i) {
   if (c->timing) cudaEventRecord(c->ev[i], c->stream);
 }
 
+// Kernel launch accounting per class (0 merge+gate, 1 Jacobi, 2 truncate, 3 split, 4 other).
+inline void count_launch(pc_circuit* c, int cls, int k = 1) { c->t_launch[cls] += k; }
+
 // One wave: factorise every task (merge, gate, Jacobi, truncate), then split the ones that
 // are committed.  `accept` (may be null) decides per task from its count; counts returned.
 struct WaveItem {
@@ -328,7 +344,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   counts.assign(T, 0);
   if (T == 0) return PC_OK;
   if (T > c->max_tasks) return fail(ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
-  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0;
+  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_len = 0;
   for (int t = 0; t < T; ++t) {
     const int j = items[t].bond;
     const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
@@ -353,11 +369,13 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     pc::JacobiTask& jt = c->h_jtasks[t];
     jt.X = u.X;
     jt.Q = u.transposed ? c->d_Q + (size_t)t * c->scratch_elems : nullptr;
+    jt.nrm2 = c->d_nrm + (size_t)t * 4 * c->chi_max;
     jt.m = u.transposed ? u.n : u.m;
     jt.n = u.transposed ? u.m : u.n;
     jt.mp = jt.m + (jt.m & 1);
     jt.pad_ = 0;
     max_m = std::max(max_m, u.m); max_n = std::max(max_n, u.n);
+    max_len = std::max(max_len, jt.n);
     max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
   }
   cudaStream_t s = c->stream;
@@ -372,9 +390,19 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, T, max_m, max_n, s));
   CUDA_TRY(ctx, pc::launch_gate_apply(c->d_tasks, T, max_cl, max_cr, s));
   CUDA_TRY(ctx, pc::launch_init_accumulators(c->d_jtasks, T, max_n, s));
+  count_launch(c, 0, 2);
+  count_launch(c, 4, 1);
+  count_launch(c, 1, 1);
+  count_launch(c, 2, 1);
+  for (int t = 0; t < T; ++t) {
+    const pc::UpdateTask& u = c->h_tasks[t];
+    c->t_flops[0] += 8.0 * u.m * (double)u.chi_m * u.n + 8.0 * 256.0 * u.chi_l * (double)u.chi_r;
+    const double M = std::max(u.m, u.n), N = std::min(u.m, u.n);
+    c->t_flops[1] += 4.0 * (4.0 * M * M * N + 22.0 * N * N * N);
+  }
   timer_mark(c, 1);
   CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
-                                  ctx->sm_count, s));
+                                  ctx->sm_count, max_len, s));
   timer_mark(c, 2);
   const int stride = 4 * c->chi_max;
   CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,
@@ -390,7 +418,6 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
     cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
     c->t_ms[0] += a; c->t_ms[1] += b; c->t_ms[2] += d;
-    c->t_launch[0] += 1; c->t_launch[1] += 1; c->t_launch[2] += 1;
   }
   if (*c->h_err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
   for (int t = 0; t < T; ++t) {
@@ -429,6 +456,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     g.lda = u.n; g.ldb = u.n; g.ldc = cnt;
     g.opB = 1; g.accumulate = 0; g.alpha = 1.0 / c->h_tout[t].nrm;
     max_cnt = std::max(max_cnt, cnt); max_nn = std::max(max_nn, u.n); max_mm = std::max(max_mm, u.m);
+    c->t_flops[3] += 8.0 * u.m * (double)u.n * cnt;
     ++nc;
   }
   if (nc > 0) {
@@ -437,6 +465,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm2, c->h_gemm2, nc * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, pc::launch_split_rows(c->d_split, nc, max_cnt, max_nn, s));
     CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm2, nc, max_mm, max_cnt, s));
+    count_launch(c, 3, 2);
     for (int t = 0; t < T; ++t) {
       if (!commit[t]) continue;
       const int j = items[t].bond;
@@ -451,7 +480,6 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
       float e = 0;
       cudaEventElapsedTime(&e, c->ev[4], c->ev[5]);
       c->t_ms[3] += e;
-      c->t_launch[3] += 1;
     }
   }
   c->stats.max_chi = std::max(c->stats.max_chi, max_bond(c));
@@ -542,6 +570,7 @@ pc_status apply_oneq_layer(pc_circuit* c) {
     const int j = c->lay[PC_SIDE_LEFT].pos[c->oneq_q[k]];
     CUDA_TRY(c->ctx, cudaMemcpyAsync(c->d_g2, &c->oneq_m[4 * k], 4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c->ctx, pc::launch_one_site(site_ptr(c, j), c->chi[j], c->chi[j + 1], c->d_g2, PC_SIDE_LEFT, c->stream));
+    count_launch(c, 4);
     CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
   }
   c->projected = false;
@@ -714,6 +743,7 @@ pc_status project(pc_circuit* c) {
       CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cr, c->stream));
       CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+      count_launch(c, 4, 2);
       c->h_gemm[0] = g2;
       CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cl, c->stream));
@@ -841,15 +871,16 @@ pc_status pc_destroy_circuit(pc_circuit* c) {
   return PC_OK;
 }
 
-pc_status pc_contract(pc_circuit* c, pc_stats* stats) {
-  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats* stats, int32_t* done) {
+  if (check_circuit(c) != PC_OK || max_iterations < 0) return PC_ERR_INVALID_ARG;
   pc_ctx* ctx = c->ctx;
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
   const double t0 = now_s();
   c->stats = pc_stats{};
   const double tau = ctx->cfg.tau;
   pc_status st = PC_OK;
-  while (layers_remain(c)) {
+  for (int32_t it = 0; it < max_iterations && layers_remain(c); ++it) {
+    // Algorithm 1: absorb layer pairs while size(M) < tau (progress rule: at least one)
     bool first = true;
     while ((first || (double)mpo_size(c) < tau) && layers_remain(c)) {
       st = absorb_layer_pair(c);
@@ -867,7 +898,71 @@ pc_status pc_contract(pc_circuit* c, pc_stats* stats) {
   c->stats.max_chi = std::max(c->stats.max_chi, max_bond(c));
   c->stats.seconds = now_s() - t0;
   if (stats) *stats = c->stats;
-  return c->stats.stalled ? PC_WARN_STALLED : PC_OK;
+  if (done) *done = layers_remain(c) ? 0 : 1;
+  return PC_OK;
+}
+
+pc_status pc_contract(pc_circuit* c, pc_stats* stats) {
+  pc_stats local{};
+  int32_t done = 0;
+  pc_status st = pc_contract_iterations(c, INT32_MAX, &local, &done);
+  if (st != PC_OK) return st;
+  if (stats) *stats = local;
+  return local.stalled ? PC_WARN_STALLED : PC_OK;
+}
+
+pc_status pc_get_cursors(pc_circuit* c, int64_t* left, int64_t* right) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  if (left) *left = (int64_t)c->lcur;
+  if (right) *right = (int64_t)c->rcur;
+  return PC_OK;
+}
+
+pc_status pc_set_cursors(pc_circuit* c, int64_t left, int64_t right) {
+  if (check_circuit(c) != PC_OK || left < 0 || right < 0 || left > (int64_t)c->left_layers.size() ||
+      right > (int64_t)c->right_layers.size())
+    return PC_ERR_INVALID_ARG;
+  c->lcur = (size_t)left;
+  c->rcur = (size_t)right;
+  c->oneq_done = c->oneq_q.empty();
+  return PC_OK;
+}
+
+pc_status pc_snapshot(pc_circuit* c) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  const size_t nsite = c->site_off[c->n], nlam = (size_t)std::max(1, c->n - 1) * c->chi_max;
+  if (!c->d_snap_sites) {
+    CUDA_TRY(ctx, cudaMalloc(&c->d_snap_sites, nsite * sizeof(double2)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_snap_lam, nlam * sizeof(double)));
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_snap_sites, c->d_sites, nsite * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_snap_lam, c->d_lam, nlam * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->snap_chi = c->chi;
+  c->snap_lay[0] = c->lay[0];
+  c->snap_lay[1] = c->lay[1];
+  c->snap_lcur = c->lcur;
+  c->snap_rcur = c->rcur;
+  c->snap_oneq_done = c->oneq_done;
+  c->has_snapshot = true;
+  return PC_OK;
+}
+
+pc_status pc_restore(pc_circuit* c) {
+  if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  if (!c->has_snapshot) return fail(c->ctx, PC_ERR_STATE, "no snapshot to restore");
+  pc_ctx* ctx = c->ctx;
+  const size_t nsite = c->site_off[c->n], nlam = (size_t)std::max(1, c->n - 1) * c->chi_max;
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_sites, c->d_snap_sites, nsite * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_lam, c->d_snap_lam, nlam * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->chi = c->snap_chi;
+  c->lay[0] = c->snap_lay[0];
+  c->lay[1] = c->snap_lay[1];
+  c->lcur = c->snap_lcur;
+  c->rcur = c->snap_rcur;
+  c->oneq_done = c->snap_oneq_done;
+  c->projected = false;
+  return PC_OK;
 }
 
 pc_status pc_unswap(pc_circuit* c, int32_t* n_accepted) {
@@ -1039,6 +1134,7 @@ pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, 
   CUDA_TRY(ctx, cudaMalloc(&pool, (size_t)cap_slots * CH * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&d_marg, 2 * sizeof(double)));
   CUDA_TRY(ctx, pc::launch_fill_ones(pool, 1, c->stream));
+  count_launch(c, 4);
   int64_t used = 1;
   heap.push(Node{1.0, {}, 0});
   int64_t expansions = 0;
@@ -1071,6 +1167,7 @@ pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, 
     double2* w1 = pool + (size_t)(used + 1) * CH;
     cudaError_t e = pc::launch_expand(pool + (size_t)top.slot * CH, site_ptr(c, j), cl, cr, c->d_env + c->env_off[j + 1],
                                       w0, w1, d_marg, c->stream);
+    count_launch(c, 4);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hm, d_marg, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { cudaFree(pool); cudaFree(d_marg); return fail(ctx, PC_ERR_CUDA, cudaGetErrorString(e)); }
@@ -1105,6 +1202,7 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
     return fail(ctx, PC_ERR_OOM, "sampling buffers");
   }
   cudaError_t e = pc::launch_fill_ones(V, rows, c->stream);
+  count_launch(c, 4);
   for (int j = 0; j < n && e == cudaSuccess; ++j) {
     const int cl = c->chi[j], cr = c->chi[j + 1];
     pc::GemmDesc g[2];
@@ -1119,6 +1217,7 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
     c->h_gemm[1] = g[1];
     e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, 2 * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 2, rows, cr, c->stream);
+    count_launch(c, 4);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) break;
     if (sampling) {
@@ -1132,12 +1231,14 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
         e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 1, rows, cr, c->stream);
         if (e == cudaSuccess) e = pc::launch_quadform_rows(q.A, Y, rows, cr, cr, sg ? m1 : m0, c->stream);
+        count_launch(c, 4, 2);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       }
       if (e == cudaSuccess) e = pc::launch_sample_pick(W0, W1, m0, m1, d_u, rows, cr, j, n, V2, d_site_bits, c->stream);
     } else {
       e = pc::launch_amp_pick(W0, W1, d_site_bits, rows, cr, j, n, V2, c->stream);
     }
+    count_launch(c, 4);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     std::swap(V, V2);
   }
@@ -1219,18 +1320,25 @@ pc_status pc_amplitudes(pc_circuit* c, int64_t k, const uint8_t* bits, double* a
   return PC_OK;
 }
 
-pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms) {
+pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops) {
   if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
   for (int k = 0; k < 5; ++k) {
     if (launches) launches[k] = c->t_launch[k];
     if (ms) ms[k] = c->t_ms[k];
+    if (flops) flops[k] = c->t_flops[k];
   }
+  return PC_OK;
+}
+
+pc_status pc_get_stream(pc_circuit* c, void** stream) {
+  if (check_circuit(c) != PC_OK || !stream) return PC_ERR_INVALID_ARG;
+  *stream = (void*)c->stream;
   return PC_OK;
 }
 
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable) {
   if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
-  for (int k = 0; k < 5; ++k) { c->t_launch[k] = 0; c->t_ms[k] = 0.0; }
+  for (int k = 0; k < 5; ++k) { c->t_launch[k] = 0; c->t_ms[k] = 0.0; c->t_flops[k] = 0.0; }
   c->timing = enable != 0;
   return PC_OK;
 }

@@ -47,6 +47,7 @@ struct UpdateTask {
 struct JacobiTask {
   double2* X;             // m x n row-major; rows are orthogonalised in place
   double2* Q;             // optional m x m accumulator (nullptr: none)
+  double* nrm2;           // m squared row norms (scratch owned by the kernel)
   int32_t m, n;
   int32_t mp;             // m rounded up to even
   int32_t pad_;
@@ -78,7 +79,7 @@ cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int 
 // caller), err = 1 int (zeroed): set to 1 if a grid barrier wait exceeded its limit.
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status,
                           int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count,
-                          cudaStream_t stream);
+                          int max_len, cudaStream_t stream);
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max,
                             int32_t* d_idx, int idx_stride, double* d_lam, double* d_sraw,
                             int lam_stride, TruncOut* d_out, cudaStream_t stream);

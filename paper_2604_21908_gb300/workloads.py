@@ -260,3 +260,46 @@ def workload_unswap28(seed: int = 0) -> Circuit:
 def workload_precision36(seed: int = 0) -> Circuit:
     """n=36 all-to-all, 400 gates per half, hidden permutation, eps=0.03."""
     return hidden_permutation_mirror(36, 400, 0.03, seed, store_complex64=True)
+
+
+def saturated_bond_dims(n: int, chi_max: int) -> list[int]:
+    """[1, 4, 16, ..., chi_max, ..., 16, 4, 1]: every bond at min(chi_max, 4^distance)."""
+    chi = [1] * (n + 1)
+    for b in range(n - 1):
+        chi[b + 1] = min(chi_max, 4 ** min(b + 1, n - 1 - b))
+    return chi
+
+
+def peaked_saturated_state(n: int, chi_max: int, seed: int = 0, delta: float = 0.02):
+    """A seeded MPO in the shape the contraction reaches on the perturbed hidden-permutation
+    workloads (every interior bond at chi_max), written as right-isometric site tensors
+    B_j[chi_{j-1}, 4, chi_j] (p = 2*out + in) and bond spectra.
+
+    Row 0 of every site is sqrt(1-delta) times the identity component (out = in, right bond
+    index 0) plus sqrt(delta) times a random unit direction orthogonal to it; the other rows
+    complete an orthonormal set.  The operator is thus the identity plus an O(delta) part on
+    every site: its output on |0...0> is peaked on 0...0.  Spectra: 1 followed by
+    sqrt(delta) exp(-k/64), normalised."""
+    rng = rng_for(11, seed)
+    chi = saturated_bond_dims(n, chi_max)
+    B = []
+    for j in range(n):
+        cl, cr = chi[j], chi[j + 1]
+        d = 4 * cr
+        e_id = np.zeros(d, dtype=np.complex128)
+        e_id[0 * cr + 0] = e_id[3 * cr + 0] = 1.0 / np.sqrt(2.0)
+        w = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+        w -= e_id * np.vdot(e_id, w)
+        w /= np.linalg.norm(w)
+        row0 = np.sqrt(1.0 - delta) * e_id + np.sqrt(delta) * w
+        z = rng.standard_normal((d, cl)) + 1j * rng.standard_normal((d, cl))
+        z[:, 0] = row0
+        q, r = np.linalg.qr(z)
+        q = q * (np.diag(r) / np.abs(np.diag(r)))[None, :]     # column 0 equals row0 exactly
+        B.append(np.ascontiguousarray(q.conj().T.reshape(cl, 4, cr)))
+    lam = []
+    for b in range(n - 1):
+        k = chi[b + 1]
+        s = np.concatenate([[1.0], np.sqrt(delta) * np.exp(-np.arange(1, k) / 64.0)])
+        lam.append(s / np.linalg.norm(s))
+    return B, lam
