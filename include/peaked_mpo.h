@@ -200,6 +200,26 @@ pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n
 pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops);
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
 
+/* One bond factorisation that allocates no device memory.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc (a program that fixes its device
+ * footprint at start-up, a plugin inside a framework that owns all device allocations,
+ * code running where allocation is not allowed).  It runs the library's one-sided Jacobi,
+ * truncation (keep s_k > eps * s_0, at most chi_max, renormalised) and V^dagger extraction
+ * on the caller's buffers, with all scratch in one fixed device array (about 2.1 MB, held
+ * by every GPU that loads the library until exit).
+ *   x_dev   DEVICE float64[m][n][2], the bond matrix, row-major; 1 <= m, n <= 256
+ *   s_dev   DEVICE float64[min(m, n, chi_max)]: kept singular values, normalised to unit 2-norm
+ *   vh_dev  DEVICE float64[min(m, n, chi_max)][n][2]: kept right singular vectors as rows
+ *   count   HOST: number of values kept
+ *   stream  a cudaStream_t, or NULL for the default stream; the call returns after it
+ *           has synchronised that stream.
+ * Sizes beyond 256 return PC_ERR_INVALID_ARG.  Every call shares the one array and leaves
+ * its contents there; calls that overlap on the GPU (concurrent streams, threads) race.
+ * The first call on a device looks up the array's address with that device current:
+ * make it before any stream capture. */
+pc_status pc_factorise_noalloc(const double* x_dev, int32_t m, int32_t n, double eps, int32_t chi_max,
+                               double* s_dev, double* vh_dev, int32_t* count, void* stream);
+
 /* The CUDA stream (a cudaStream_t) every kernel of this circuit runs on, for callers that
  * time or order their own work against it.  The circuit keeps ownership. */
 pc_status pc_get_stream(pc_circuit* c, void** stream);

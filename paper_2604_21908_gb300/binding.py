@@ -50,7 +50,7 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_get_bond_dims", "pc_get_layouts", "pc_get_spectrum", "pc_get_site", "pc_set_state",
            "pc_apply_updates", "pc_plan_routing", "pc_get_plan", "pc_get_unswap_log", "pc_kernel_timers",
            "pc_reset_kernel_timers", "pc_contract_iterations", "pc_get_cursors", "pc_set_cursors", "pc_snapshot",
-           "pc_restore", "pc_get_stream"]
+           "pc_restore", "pc_get_stream", "pc_factorise_noalloc"]
 
 
 def _p(t):
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "pc_snapshot": ([vp], i32),
         "pc_restore": ([vp], i32),
         "pc_get_stream": ([vp, _p(vp)], i32),
+        "pc_factorise_noalloc": ([vp, i32, i32, dbl, i32, vp, vp, _p(i32), vp], i32),
         "pc_reset_kernel_timers": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -134,6 +135,19 @@ def plan_routing(n_qubits: int, pairs: np.ndarray, split_index: int) -> np.ndarr
     if st != PC_OK:
         raise PcError(st, "pc_plan_routing")
     return rec[: n_rec.value]
+
+
+def factorise_noalloc(x_ptr: int, m: int, n: int, eps: float, chi_max: int, s_ptr: int, vh_ptr: int,
+                      stream: int = 0) -> int:
+    """pc_factorise_noalloc on caller-owned device buffers (addresses as integers); returns
+    the number of kept values."""
+    lib = load()
+    k = C.c_int32(0)
+    st = lib.pc_factorise_noalloc(C.c_void_p(x_ptr), m, n, eps, chi_max, C.c_void_p(s_ptr), C.c_void_p(vh_ptr),
+                                  C.byref(k), C.c_void_p(stream) if stream else None)
+    if st != PC_OK:
+        raise PcError(st, "pc_factorise_noalloc")
+    return k.value
 
 
 class Context:
