@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
   __shared__ int s_off[JAC_MAX_TASKS + 1];
   __shared__ unsigned char s_done[JAC_MAX_TASKS];
   __shared__ double s_red[2][NG][G][4];
+  __shared__ double s_rot[NG][8];
   if (threadIdx.x == 0) {
     int off = 0;
     for (int t = 0; t < ntasks; ++t) { s_off[t] = off; off += tasks[t].mp >> 1; }
@@ -236,7 +237,9 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
   for (int t = threadIdx.x; t < ntasks; t += blockDim.x) s_done[t] = 0;
   __syncthreads();
   const int grp = threadIdx.x / GT, gl = threadIdx.x % GT;
-  const int ggrp = blockIdx.x * NG + grp, ngrp = gridDim.x * NG;
+  // consecutive pairs go to consecutive CTAs, so a round with fewer pairs than groups still
+  // spreads over every SM
+  const int ggrp = grp * gridDim.x + blockIdx.x, ngrp = gridDim.x * NG;
   const int total = s_off[ntasks];
   const double eps64 = 2.220446049250313e-16;
   int parity = 0;
@@ -329,28 +332,56 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
       }
       group_sum4<G>(aa, bb, gr, gi, red, grp, gl);
       parity ^= 1;
-      if (!full) { aa = tk.nrm2[a]; bb = tk.nrm2[b]; }
-      // rows at the underflow floor are zero for every purpose here
-      bool rotate = !(aa < 1e-280 || bb < 1e-280);
-      const double gabs = hypot(gr, gi);
-      const double tol = 2.0 * eps64 * sqrt((double)n);
-      rotate = rotate && (gabs > tol * sqrt(aa) * sqrt(bb));
+      // The rotation's scalars cost the same FP64 pipe time on every warp that computes them
+      // (whatever its active lanes), so only the group's first warp does; it shares them
+      // through shared memory.  Scalars: |g|^2 against tol^2 a b (no square roots),
+      // zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+      // c = 1/sqrt(1 + t^2), s = c t, e = conj(g)/|g|.
+      Rot q;
+      double tg = 0.0;                        // t |g|, for the norm update
+      int rotate;
+      if (G == 1 || gl < 32) {
+        if (!full) { aa = tk.nrm2[a]; bb = tk.nrm2[b]; }
+        const double g2 = fma(gr, gr, gi * gi);
+        const double tol = 2.0 * eps64 * sqrt((double)n);
+        // rows at the underflow floor are zero for every purpose here
+        rotate = !(aa < 1e-280 || bb < 1e-280) && (g2 > (tol * tol) * aa * bb);
+        if (rotate) {
+          const double gabs = sqrt(g2);
+          const double inv_g = 1.0 / gabs;
+          const double zeta = 0.5 * (bb - aa) * inv_g;
+          double tt;
+          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
+          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          q.c = rsqrt(fma(tt, tt, 1.0));
+          q.sn = q.c * tt;
+          const double ex = gr * inv_g, ey = -gi * inv_g;   // e^{-i phi}
+          q.wx = q.sn * ex; q.wy = q.sn * ey;               // s e^{-i phi}
+          q.zx = q.c * ex; q.zy = q.c * ey;                 // c e^{-i phi}
+          tg = tt * gabs;
+        }
+        if constexpr (G > 1) {
+          if (gl == 0) {
+            double* sh = s_rot[grp];
+            sh[0] = rotate ? 1.0 : 0.0;
+            sh[1] = q.c; sh[2] = q.sn; sh[3] = q.wx; sh[4] = q.wy; sh[5] = q.zx; sh[6] = q.zy;
+          }
+        }
+      }
+      if constexpr (G > 1) {
+        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
+        if (gl >= 32) {
+          const double* sh = s_rot[grp];
+          rotate = sh[0] != 0.0;
+          q.c = sh[1]; q.sn = sh[2]; q.wx = sh[3]; q.wy = sh[4]; q.zx = sh[5]; q.zy = sh[6];
+        }
+        // the next write of s_rot comes after the next reduction's barrier, which every warp
+        // of the group reaches only after reading these values
+      }
       if (!rotate) {
         if (full && gl == 0) { tk.nrm2[a] = aa; tk.nrm2[b] = bb; }
         continue;
       }
-      // Real rotation on the phase-adjusted pair: zeta = (b - a) / (2|g|),
-      // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t.
-      const double zeta = (bb - aa) / (2.0 * gabs);
-      double tt;
-      if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
-      else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      Rot q;
-      q.c = 1.0 / sqrt(1.0 + tt * tt);
-      q.sn = q.c * tt;
-      const double ex = gr / gabs, ey = -gi / gabs;        // e^{-i phi}
-      q.wx = q.sn * ex; q.wy = q.sn * ey;                  // s e^{-i phi}
-      q.zx = q.c * ex; q.zy = q.c * ey;                    // c e^{-i phi}
       if (in_regs) {
 #pragma unroll
         for (int e = 0; e < JAC_E; ++e) {
@@ -380,8 +411,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
         }
       }
       if (gl == 0) {
-        tk.nrm2[a] = aa - tt * gabs;
-        tk.nrm2[b] = bb + tt * gabs;
+        tk.nrm2[a] = aa - tg;
+        tk.nrm2[b] = bb + tg;
         atomicAdd(&st[t].rot[s % 3], 1u);
       }
     }
@@ -651,12 +682,17 @@ cudaError_t launch_jacobi_g(const JacobiTask* d_tasks, int ntasks, JacobiStatus*
 }
 
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
-                          unsigned int* d_bar, int* d_err, int sm_count, int max_len, cudaStream_t stream) {
+                          unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
+                          cudaStream_t stream) {
   if (ntasks <= 0) return cudaSuccess;
   if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
-  // group width: enough threads to hold the longest row in registers, at most 4 warps
-  if (max_len <= 32 * JAC_E) return launch_jacobi_g<1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
-  if (max_len <= 64 * JAC_E) return launch_jacobi_g<2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  // Group width: at least enough threads to hold the longest row in registers; wider (up to
+  // four warps per pair) when a round has fewer pairs than the grid has warps.
+  const int warps = sm_count * (JAC_THREADS / 32);
+  int g = max_len <= 32 * JAC_E ? 1 : (max_len <= 64 * JAC_E ? 2 : 4);
+  while (g < 4 && total_pairs > 0 && (long long)total_pairs * 2 * g <= warps) g *= 2;
+  if (g == 1) return launch_jacobi_g<1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  if (g == 2) return launch_jacobi_g<2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
   return launch_jacobi_g<4>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
 }
 

@@ -125,7 +125,8 @@ extern "C" pc_status pc_factorise_noalloc(const double* x_dev, int32_t m, int32_
       scr, reinterpret_cast<const double2*>(x_dev), m, n, transposed);
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   if (pc::launch_init_accumulators(&scr->jtask, 1, nvec, st) != cudaSuccess) return PC_ERR_CUDA;
-  if (pc::launch_jacobi(&scr->jtask, 1, &scr->jst, NA_MAX_SWEEPS, scr->bar, &scr->err, sms, len, st) != cudaSuccess)
+  if (pc::launch_jacobi(&scr->jtask, 1, &scr->jst, NA_MAX_SWEEPS, scr->bar, &scr->err, sms, len, (nvec + 1) / 2,
+                       st) != cudaSuccess)
     return PC_ERR_CUDA;
   if (pc::launch_truncate(&scr->jtask, 1, eps, keep_max, scr->idx, 0, scr->lam, scr->sraw, 0, &scr->tout, st) !=
       cudaSuccess)

@@ -344,7 +344,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   counts.assign(T, 0);
   if (T == 0) return PC_OK;
   if (T > c->max_tasks) return fail(ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
-  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_len = 0;
+  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_len = 0, total_pairs = 0;
   for (int t = 0; t < T; ++t) {
     const int j = items[t].bond;
     const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
@@ -376,6 +376,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     jt.pad_ = 0;
     max_m = std::max(max_m, u.m); max_n = std::max(max_n, u.n);
     max_len = std::max(max_len, jt.n);
+    total_pairs += jt.mp / 2;
     max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
   }
   cudaStream_t s = c->stream;
@@ -402,7 +403,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   }
   timer_mark(c, 1);
   CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
-                                  ctx->sm_count, max_len, s));
+                                  ctx->sm_count, max_len, total_pairs, s));
   timer_mark(c, 2);
   const int stride = 4 * c->chi_max;
   CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,

@@ -77,9 +77,10 @@ cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi
 cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 // Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the
 // caller), err = 1 int (zeroed): set to 1 if a grid barrier wait exceeded its limit.
+// total_pairs = sum over tasks of mp/2 (pairs per round); it sets the group width.
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status,
                           int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count,
-                          int max_len, cudaStream_t stream);
+                          int max_len, int total_pairs, cudaStream_t stream);
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max,
                             int32_t* d_idx, int idx_stride, double* d_lam, double* d_sraw,
                             int lam_stride, TruncOut* d_out, cudaStream_t stream);
