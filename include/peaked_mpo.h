@@ -70,6 +70,10 @@ typedef struct pc_config {
   int32_t unswap_mode;       /* PC_UNSWAP_*                                               */
   int32_t jacobi_max_sweeps; /* cap on one-sided Jacobi sweeps per factorisation (>= 1)   */
   int32_t device;            /* CUDA device ordinal                                       */
+  int32_t fp32_precondition; /* 1: bond matrices with >= 64 vectors first run FP32 Jacobi  */
+                             /* sweeps; the accumulated rotation is made unitary in FP64   */
+                             /* (two Newton-Schulz steps) and applied, then FP64 sweeps    */
+                             /* finish.  The result keeps FP64 accuracy.  0: FP64 only.     */
 } pc_config;
 
 /* Counters filled by pc_contract. */
@@ -83,7 +87,8 @@ typedef struct pc_stats {
   int32_t max_chi;           /* largest bond dimension seen                               */
   int32_t stalled;           /* 1 if PC_WARN_STALLED was raised                           */
   int32_t max_sweeps;        /* largest Jacobi sweep count used by one factorisation      */
-  int32_t pad_;
+  int32_t fallbacks;         /* waves redone in FP64 only after a failed norm check of   */
+                             /* the FP32 preconditioning                                  */
   double seconds;            /* host wall time of the call                                */
 } pc_stats;
 

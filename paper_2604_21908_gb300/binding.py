@@ -24,13 +24,13 @@ UNSWAP_PARALLEL, UNSWAP_SEQUENTIAL, UNSWAP_OFF = 0, 1, 2
 class PcConfig(C.Structure):
     _fields_ = [("eps", C.c_double), ("chi_max", C.c_int32), ("tau", C.c_double),
                 ("max_unswap_iter", C.c_int32), ("accept_equal", C.c_int32), ("unswap_mode", C.c_int32),
-                ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32)]
+                ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32), ("fp32_precondition", C.c_int32)]
 
 
 class PcStats(C.Structure):
     _fields_ = [("n_updates", C.c_int64), ("n_trials", C.c_int64), ("n_accepted", C.c_int64),
                 ("n_stages", C.c_int64), ("n_waves", C.c_int64), ("final_size", C.c_int64),
-                ("max_chi", C.c_int32), ("stalled", C.c_int32), ("max_sweeps", C.c_int32), ("pad_", C.c_int32),
+                ("max_chi", C.c_int32), ("stalled", C.c_int32), ("max_sweeps", C.c_int32), ("fallbacks", C.c_int32),
                 ("seconds", C.c_double)]
 
     def as_dict(self):

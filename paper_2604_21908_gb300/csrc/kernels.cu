@@ -111,7 +111,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
       if (gc >= d.N) continue;
       double2 v = make_double2(d.alpha * acc[i][j].x, d.alpha * acc[i][j].y);
       double2* cp = d.C + (size_t)gr * d.ldc + gc;
-      if (d.accumulate) { const double2 o = *cp; v.x += o.x; v.y += o.y; }
+      if (d.beta != 0.0) {
+        const double2 o = d.D ? d.D[(size_t)gr * d.ldc + gc] : *cp;
+        v.x = fma(d.beta, o.x, v.x);
+        v.y = fma(d.beta, o.y, v.y);
+      }
       *cp = v;
     }
   }
@@ -178,14 +182,41 @@ constexpr int JAC_MAX_TASKS = 256;
 constexpr int JAC_THREADS = 512;
 constexpr int JAC_E = 8;            // row elements per thread held in registers
 
-// Rotates one pair of rows of length len held by a group of GT threads: either in registers
-// (len <= GT * JAC_E) or streamed from memory.
-struct Rot {
-  double c, sn, wx, wy, zx, zy;
+// Element and task types of the Jacobi kernel in FP64 (the factorisation) and FP32 (the
+// preconditioning sweeps).
+template <typename R> struct JacTraits;
+template <> struct JacTraits<double> {
+  using C = double2;
+  using Task = JacobiTask;
+  static constexpr double eps = 2.220446049250313e-16;   // 2^-52
+  static constexpr double tiny = 1e-280;                   // floor for squared row norms
+  static constexpr double g2min = 1e-290;                  // |g|^2 below this is not rotated
+  static constexpr double huge = 1e100;
+};
+template <> struct JacTraits<float> {
+  using C = float2;
+  using Task = JacobiTask32;
+  static constexpr float eps = 1.1920929e-7f;              // 2^-23
+  // Rows of a normalised bond matrix below 1e-15 in norm, and inner products whose square
+  // would be subnormal in FP32 (where |g| / sqrt(g^2) is no longer 1 to FP32 precision and
+  // the rotation would stop being unitary), are left to the FP64 sweeps.
+  static constexpr float tiny = 1e-30f;
+  static constexpr float g2min = 1e-36f;
+  static constexpr float huge = 1e18f;
 };
 
-__device__ __forceinline__ void rot_apply(const Rot& q, double2& u, double2& v) {
-  double2 na, nb;
+__device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mk2(float x, float y) { return make_float2(x, y); }
+
+template <typename R>
+struct Rot {
+  R c, sn, wx, wy, zx, zy;
+};
+
+// [u, v] <- [c u - s e v, s u + c e v] with e = e^{-i phi} (exactly unitary for c^2+s^2=1, |e|=1)
+template <typename R, typename C>
+__device__ __forceinline__ void rot_apply(const Rot<R>& q, C& u, C& v) {
+  C na, nb;
   na.x = q.c * u.x - (q.wx * v.x - q.wy * v.y);
   na.y = q.c * u.y - (q.wx * v.y + q.wy * v.x);
   nb.x = q.sn * u.x + (q.zx * v.x - q.zy * v.y);
@@ -194,62 +225,77 @@ __device__ __forceinline__ void rot_apply(const Rot& q, double2& u, double2& v) 
   v = nb;
 }
 
+template <typename R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum of four values over the GT threads of a group, identical on every thread.
-template <int G>
-__device__ __forceinline__ void group_sum4(double& a, double& b, double& c, double& d, double (*red)[4],
-                                           int grp, int gl) {
-  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c); d = warp_sum(d);
+template <typename R, int G>
+__device__ __forceinline__ void group_sum4(R& a, R& b, R& c, R& d, R (*red)[4], int grp, int gl) {
+  a = warp_sum_t(a); b = warp_sum_t(b); c = warp_sum_t(c); d = warp_sum_t(d);
   if constexpr (G > 1) {
     const int w = gl >> 5;
     if ((gl & 31) == 0) { red[w][0] = a; red[w][1] = b; red[w][2] = c; red[w][3] = d; }
     asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
-    a = b = c = d = 0.0;
+    a = b = c = d = R(0);
 #pragma unroll
     for (int k = 0; k < G; ++k) { a += red[k][0]; b += red[k][1]; c += red[k][2]; d += red[k][3]; }
   }
 }
 
 // One-sided (Hestenes) Jacobi on the rows of each task's matrix: rotate pairs of rows until
-// every pair is orthogonal to |<x_a, x_b>| <= tol |x_a| |x_b|, tol = 2 eps_64 sqrt(n).
-// Pairs follow the round-robin (circle) ordering: in round r of a sweep over mp rows,
-// pair 0 = (mp-1, r), pair i = ((r+i) mod (mp-1), (r-i) mod (mp-1)).  Each global iteration
-// runs one round of every unfinished task (tasks of different sizes advance their own
-// sweeps), then all CTAs meet at a grid barrier.  A group of G warps rotates one pair.
+// every pair is orthogonal to |<x_a, x_b>| <= tol |x_a| |x_b|, tol = 2 eps sqrt(n) (eps the
+// unit roundoff of R).  Pairs follow the round-robin (circle) ordering: in round r of a sweep
+// over mp rows, pair 0 = (mp-1, r), pair i = ((r+i) mod (mp-1), (r-i) mod (mp-1)).  Each
+// global iteration runs one round of every unfinished task (tasks of different sizes advance
+// their own sweeps), then all CTAs meet at a grid barrier.  A group of G warps rotates one pair.
 // Squared row norms are computed exactly in round 0 of every sweep and carried through the
 // sweep with the exact-arithmetic update a' = a - t|g|, b' = b + t|g|; a sweep with no
 // rotation leaves them untouched, so the convergence decision always uses exact norms.
-template <int G>
-__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask* __restrict__ tasks,
+template <typename R, int G>
+__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename JacTraits<R>::Task* __restrict__ tasks,
                                                                int ntasks, JacobiStatus* st,
                                                                int max_sweeps, unsigned int* bar,
                                                                int* err) {
+  using C = typename JacTraits<R>::C;
+  using Task = typename JacTraits<R>::Task;
   constexpr int GT = 32 * G;
   constexpr int NG = JAC_THREADS / GT;
   __shared__ int s_off[JAC_MAX_TASKS + 1];
   __shared__ unsigned char s_done[JAC_MAX_TASKS];
-  __shared__ double s_red[2][NG][G][4];
-  __shared__ double s_rot[NG][8];
+  __shared__ Task s_task[JAC_MAX_TASKS];
+  __shared__ R s_red[2][NG][G][4];
+  __shared__ R s_rot[NG][8];
+  __shared__ R s_dead2[JAC_MAX_TASKS];
+  for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
+    s_done[t] = 0;
+    s_task[t] = tasks[t];
+    s_dead2[t] = s_task[t].fro2 ? (R)(s_task[t].dead_rel * *s_task[t].fro2) : R(0);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int off = 0;
-    for (int t = 0; t < ntasks; ++t) { s_off[t] = off; off += tasks[t].mp >> 1; }
+    for (int t = 0; t < ntasks; ++t) { s_off[t] = off; off += s_task[t].mp >> 1; }
     s_off[ntasks] = off;
   }
-  for (int t = threadIdx.x; t < ntasks; t += blockDim.x) s_done[t] = 0;
   __syncthreads();
   const int grp = threadIdx.x / GT, gl = threadIdx.x % GT;
   // consecutive pairs go to consecutive CTAs, so a round with fewer pairs than groups still
   // spreads over every SM
   const int ggrp = grp * gridDim.x + blockIdx.x, ngrp = gridDim.x * NG;
   const int total = s_off[ntasks];
-  const double eps64 = 2.220446049250313e-16;
+  const R eps = JacTraits<R>::eps;
   int parity = 0;
 
   for (long long g = 0;; ++g) {
     for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
       if (s_done[t]) continue;
-      const long long R = tasks[t].mp - 1;
-      const long long s = g / R;
-      const long long r = g - s * R;
+      const long long Rr = s_task[t].mp - 1;
+      const long long s = g / Rr;
+      const long long r = g - s * Rr;
       if (r == 0 && s > 0) {
         const unsigned int rc = *(volatile unsigned int*)&st[t].rot[(s - 1) % 3];
         if (rc == 0 || s >= max_sweeps) {
@@ -273,45 +319,48 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
       }
       const int t = lo;
       if (s_done[t]) continue;
-      const JacobiTask tk = tasks[t];
-      const int R = tk.mp - 1;
-      const long long s = g / R;
-      const int r = (int)(g - s * R);
+      const Task& tk = s_task[t];
+      const int Rr = tk.mp - 1;
+      const long long s = g / Rr;
+      const int r = (int)(g - s * Rr);
       const int i = item - s_off[t];
       int a, b;
       if (i == 0) { a = tk.mp - 1; b = r; }
-      else { a = (r + i) % R; b = (r - i + R) % R; }
+      else { a = (r + i) % Rr; b = (r - i + Rr) % Rr; }
       const bool full = (r == 0);
-      double (*red)[4] = s_red[parity][grp];
+      R (*red)[4] = s_red[parity][grp];
       if (a >= tk.m || b >= tk.m) {
         // the padding row: in round 0 the real row still gets its exact norm
         if (full) {
           const int v = a < tk.m ? a : b;
-          const double2* xv = tk.X + (size_t)v * tk.n;
-          double acc = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+          const C* xv = tk.X + (size_t)v * tk.n;
+          R acc = R(0), z1 = R(0), z2 = R(0), z3 = R(0);
           for (int k = gl; k < tk.n; k += GT) acc = fma(xv[k].x, xv[k].x, fma(xv[k].y, xv[k].y, acc));
-          group_sum4<G>(acc, z1, z2, z3, red, grp, gl);
+          group_sum4<R, G>(acc, z1, z2, z3, red, grp, gl);
           if (gl == 0) tk.nrm2[v] = acc;
           parity ^= 1;
         }
         continue;
       }
-      double2* xa = tk.X + (size_t)a * tk.n;
-      double2* xb = tk.X + (size_t)b * tk.n;
+      C* xa = tk.X + (size_t)a * tk.n;
+      C* xb = tk.X + (size_t)b * tk.n;
       const int n = tk.n;
+      // the carried norms, fetched early so their latency overlaps the row loads
+      R na_pre = R(0), nb_pre = R(0);
+      if (!full && (G == 1 || gl < 32)) { na_pre = tk.nrm2[a]; nb_pre = tk.nrm2[b]; }
       const bool in_regs = n <= GT * JAC_E;
-      double2 ra[JAC_E], rb[JAC_E];
-      double aa = 0.0, bb = 0.0, gr = 0.0, gi = 0.0;
+      C ra[JAC_E], rb[JAC_E];
+      R aa = R(0), bb = R(0), gr = R(0), gi = R(0);
       if (in_regs) {
 #pragma unroll
         for (int e = 0; e < JAC_E; ++e) {
           const int k = gl + e * GT;
-          ra[e] = k < n ? xa[k] : make_double2(0.0, 0.0);
-          rb[e] = k < n ? xb[k] : make_double2(0.0, 0.0);
+          ra[e] = k < n ? xa[k] : mk2(R(0), R(0));
+          rb[e] = k < n ? xb[k] : mk2(R(0), R(0));
         }
 #pragma unroll
         for (int e = 0; e < JAC_E; ++e) {
-          const double2 u = ra[e], v = rb[e];
+          const C u = ra[e], v = rb[e];
           gr = fma(u.x, v.x, fma(u.y, v.y, gr));
           gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
           if (full) {
@@ -321,7 +370,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
         }
       } else {
         for (int k = gl; k < n; k += GT) {
-          const double2 u = xa[k], v = xb[k];
+          const C u = xa[k], v = xb[k];
           gr = fma(u.x, v.x, fma(u.y, v.y, gr));
           gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
           if (full) {
@@ -330,40 +379,44 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
           }
         }
       }
-      group_sum4<G>(aa, bb, gr, gi, red, grp, gl);
+      group_sum4<R, G>(aa, bb, gr, gi, red, grp, gl);
       parity ^= 1;
-      // The rotation's scalars cost the same FP64 pipe time on every warp that computes them
+      // The rotation's scalars cost the same pipe time on every warp that computes them
       // (whatever its active lanes), so only the group's first warp does; it shares them
       // through shared memory.  Scalars: |g|^2 against tol^2 a b (no square roots),
       // zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
       // c = 1/sqrt(1 + t^2), s = c t, e = conj(g)/|g|.
-      Rot q;
-      double tg = 0.0;                        // t |g|, for the norm update
+      Rot<R> q;
+      R tg = R(0);                            // t |g|, for the norm update
       int rotate;
       if (G == 1 || gl < 32) {
-        if (!full) { aa = tk.nrm2[a]; bb = tk.nrm2[b]; }
-        const double g2 = fma(gr, gr, gi * gi);
-        const double tol = 2.0 * eps64 * sqrt((double)n);
+        if (!full) { aa = na_pre; bb = nb_pre; }
+        const R g2 = fma(gr, gr, gi * gi);
+        const R tol = R(2) * eps * sqrt(R(n));
         // rows at the underflow floor are zero for every purpose here
-        rotate = !(aa < 1e-280 || bb < 1e-280) && (g2 > (tol * tol) * aa * bb);
+        const R dead2 = s_dead2[t];
+        rotate = !(aa < JacTraits<R>::tiny || bb < JacTraits<R>::tiny) && !(aa < dead2 && bb < dead2) &&
+                 g2 >= JacTraits<R>::g2min && (g2 > (tol * tol) * aa * bb);
         if (rotate) {
-          const double gabs = sqrt(g2);
-          const double inv_g = 1.0 / gabs;
-          const double zeta = 0.5 * (bb - aa) * inv_g;
-          double tt;
-          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
-          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          q.c = rsqrt(fma(tt, tt, 1.0));
+          const R gabs = sqrt(g2);
+          const R inv_g = R(1) / gabs;
+          const R zeta = R(0.5) * (bb - aa) * inv_g;
+          R tt;
+          if (fabs(zeta) > JacTraits<R>::huge) tt = R(0.5) / zeta;
+          else tt = copysign(R(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, R(1))));
+          // correctly rounded 1/sqrt: an approximate reciprocal square root has a one-signed
+          // error that compounds over the tens of thousands of rotations a row takes part in
+          q.c = R(1) / sqrt(fma(tt, tt, R(1)));
           q.sn = q.c * tt;
-          const double ex = gr * inv_g, ey = -gi * inv_g;   // e^{-i phi}
+          const R ex = gr * inv_g, ey = -gi * inv_g;        // e^{-i phi}
           q.wx = q.sn * ex; q.wy = q.sn * ey;               // s e^{-i phi}
           q.zx = q.c * ex; q.zy = q.c * ey;                 // c e^{-i phi}
           tg = tt * gabs;
         }
         if constexpr (G > 1) {
           if (gl == 0) {
-            double* sh = s_rot[grp];
-            sh[0] = rotate ? 1.0 : 0.0;
+            R* sh = s_rot[grp];
+            sh[0] = rotate ? R(1) : R(0);
             sh[1] = q.c; sh[2] = q.sn; sh[3] = q.wx; sh[4] = q.wy; sh[5] = q.zx; sh[6] = q.zy;
           }
         }
@@ -371,8 +424,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
       if constexpr (G > 1) {
         asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
         if (gl >= 32) {
-          const double* sh = s_rot[grp];
-          rotate = sh[0] != 0.0;
+          const R* sh = s_rot[grp];
+          rotate = sh[0] != R(0);
           q.c = sh[1]; q.sn = sh[2]; q.wx = sh[3]; q.wy = sh[4]; q.zx = sh[5]; q.zy = sh[6];
         }
         // the next write of s_rot comes after the next reduction's barrier, which every warp
@@ -394,17 +447,17 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
         }
       } else {
         for (int k = gl; k < n; k += GT) {
-          double2 u = xa[k], v = xb[k];
+          C u = xa[k], v = xb[k];
           rot_apply(q, u, v);
           xa[k] = u;
           xb[k] = v;
         }
       }
       if (tk.Q) {
-        double2* qa = tk.Q + (size_t)a * tk.m;
-        double2* qb = tk.Q + (size_t)b * tk.m;
+        C* qa = tk.Q + (size_t)a * tk.m;
+        C* qb = tk.Q + (size_t)b * tk.m;
         for (int k = gl; k < tk.m; k += GT) {
-          double2 u = qa[k], v = qb[k];
+          C u = qa[k], v = qb[k];
           rot_apply(q, u, v);
           qa[k] = u;
           qb[k] = v;
@@ -418,6 +471,46 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const JacobiTask
     }
     if (!grid_barrier(bar, err, gridDim.x)) return;
   }
+}
+
+// FP32 preconditioning set-up: X32 = float(X) row by row (the FP64 task's layout), Q32 = I.
+__global__ void precond_init_kernel(const JacobiTask* __restrict__ t64, const JacobiTask32* __restrict__ t32) {
+  const JacobiTask a = t64[blockIdx.y];
+  const JacobiTask32 b = t32[blockIdx.y];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)a.m * a.n) {
+    const double2 v = a.X[e];
+    b.X[e] = make_float2((float)v.x, (float)v.y);
+  }
+  if (e < (long long)a.m * a.m) {
+    const int i = (int)(e / a.m), j = (int)(e % a.m);
+    b.Q[e] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+  }
+}
+
+// Squared Frobenius norm of each task's FP64 matrix (fixed-order block reduction).
+__global__ void __launch_bounds__(1024) fro2_kernel(const JacobiTask* __restrict__ t64, double* out) {
+  __shared__ double red[32];
+  const JacobiTask a = t64[blockIdx.x];
+  const long long cells = (long long)a.m * a.n;
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < cells; e += blockDim.x) acc = fma(a.X[e].x, a.X[e].x, fma(a.X[e].y, a.X[e].y, acc));
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+__global__ void widen_q_kernel(const JacobiTask32* __restrict__ t32, double2* const* __restrict__ q64) {
+  const JacobiTask32 b = t32[blockIdx.y];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)b.m * b.m) return;
+  const float2 v = b.Q[e];
+  q64[blockIdx.y][e] = make_double2((double)v.x, (double)v.y);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -492,6 +585,18 @@ __global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __rest
   }
   __syncthreads();
   const double nrm = sqrt(red[0]);
+  __syncthreads();
+  double all = 0.0;
+  for (int i = threadIdx.x; i < t.m; i += blockDim.x) all = fma(sv[i], sv[i], all);
+  all = warp_sum(all);
+  if (lane == 0) red[warp] = all;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < nw ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) red[1] = v;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < count; k += blockDim.x) {
     idx_out[(size_t)blockIdx.x * idx_stride + k] = id[k];
     lam_out[(size_t)blockIdx.x * lam_stride + k] = sv[k] / nrm;
@@ -504,6 +609,7 @@ __global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __rest
     o.s0 = s0;
     o.nrm = nrm;
     o.s_first_dropped = count < t.m ? sv[count] : 0.0;
+    o.total2 = red[1];
     out[blockIdx.x] = o;
   }
 }
@@ -665,12 +771,12 @@ cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int 
   return cudaGetLastError();
 }
 
-template <int G>
-cudaError_t launch_jacobi_g(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
-                            unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
+template <typename R, int G>
+cudaError_t launch_jacobi_g(const typename JacTraits<R>::Task* d_tasks, int ntasks, JacobiStatus* d_status,
+                            int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel<G>, JAC_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel<R, G>, JAC_THREADS, 0);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm > 1) blocks_per_sm = 1;
     if (blocks_per_sm < 1) return cudaErrorLaunchOutOfResources;
@@ -678,22 +784,61 @@ cudaError_t launch_jacobi_g(const JacobiTask* d_tasks, int ntasks, JacobiStatus*
   const int grid = sm_count * blocks_per_sm;
   void* args[] = {(void*)&d_tasks, (void*)&ntasks, (void*)&d_status, (void*)&max_sweeps, (void*)&d_bar,
                   (void*)&d_err};
-  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<G>, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<R, G>, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+}
+
+// Group width: at least enough threads to hold the longest row in registers; wider (up to
+// four warps per pair) when a round has fewer pairs than the grid has warps.
+template <typename R>
+cudaError_t launch_jacobi_t(const typename JacTraits<R>::Task* d_tasks, int ntasks, JacobiStatus* d_status,
+                            int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count, int max_len,
+                            int total_pairs, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
+  const int warps = sm_count * (JAC_THREADS / 32);
+  int g = max_len <= 32 * JAC_E ? 1 : (max_len <= 64 * JAC_E ? 2 : 4);
+  while (g < 4 && total_pairs > 0 && (long long)total_pairs * 2 * g <= warps) g *= 2;
+  if (g == 1) return launch_jacobi_g<R, 1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  if (g == 2) return launch_jacobi_g<R, 2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  return launch_jacobi_g<R, 4>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
 }
 
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
                           unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
                           cudaStream_t stream) {
+  return launch_jacobi_t<double>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, max_len,
+                                 total_pairs, stream);
+}
+
+cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                            unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
+                            cudaStream_t stream) {
+  return launch_jacobi_t<float>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, max_len,
+                                total_pairs, stream);
+}
+
+cudaError_t launch_precond_init(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m, int max_n,
+                                cudaStream_t stream) {
   if (ntasks <= 0) return cudaSuccess;
-  if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
-  // Group width: at least enough threads to hold the longest row in registers; wider (up to
-  // four warps per pair) when a round has fewer pairs than the grid has warps.
-  const int warps = sm_count * (JAC_THREADS / 32);
-  int g = max_len <= 32 * JAC_E ? 1 : (max_len <= 64 * JAC_E ? 2 : 4);
-  while (g < 4 && total_pairs > 0 && (long long)total_pairs * 2 * g <= warps) g *= 2;
-  if (g == 1) return launch_jacobi_g<1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
-  if (g == 2) return launch_jacobi_g<2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
-  return launch_jacobi_g<4>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
+  const long long cells = (long long)max_m * (max_n > max_m ? max_n : max_m);
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  precond_init_kernel<<<grid, 256, 0, stream>>>(d_t64, d_t32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fro2(const JacobiTask* d_t64, int ntasks, double* d_out, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  fro2_kernel<<<ntasks, 1024, 0, stream>>>(d_t64, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_q(const JacobiTask32* d_t32, double2* const* d_q64, int ntasks, int max_m,
+                           cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_m * max_m;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  widen_q_kernel<<<grid, 256, 0, stream>>>(d_t32, d_q64);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max, int32_t* d_idx,

@@ -53,6 +53,8 @@ __global__ void noalloc_setup_kernel(NoAllocScratch* s, int m, int n, int transp
   t.X = s->X;
   t.Q = transposed ? s->Q : nullptr;
   t.nrm2 = s->nrm2;
+  t.fro2 = nullptr;
+  t.dead_rel = 0.0;
   t.m = transposed ? n : m;
   t.n = transposed ? m : n;
   t.mp = t.m + (t.m & 1);

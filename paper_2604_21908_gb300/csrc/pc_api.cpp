@@ -151,6 +151,23 @@ struct pc_circuit {
   double2* d_X = nullptr;
   double2* d_T0 = nullptr;
   double2* d_Q = nullptr;         // Jacobi accumulators (transposed path)
+  // FP32 preconditioning scratch (per task)
+  float2* d_X32 = nullptr;
+  float2* d_Q32 = nullptr;
+  double2* d_Qb = nullptr;
+  double2* d_Y = nullptr;
+  pc::JacobiTask32* d_jt32 = nullptr;
+  double2** d_q64ptr = nullptr;
+  pc::GemmDesc* d_ns = nullptr;   // 5 GEMM stages x tasks
+  pc::JacobiTask32* h_jt32 = nullptr;
+  double2** h_q64ptr = nullptr;
+  pc::GemmDesc* h_ns = nullptr;
+  // Descriptors for the FP64 sweeps after preconditioning.  A pinned staging buffer is never
+  // rewritten while an asynchronous copy from it may still be pending, so this phase has its
+  // own buffer instead of patching h_jtasks.
+  pc::JacobiTask* h_jtasks_y = nullptr;
+  double* d_xfro2 = nullptr;
+  double* h_xfro2 = nullptr;
   double* d_nrm = nullptr;        // Jacobi squared row norms
   size_t scratch_elems = 0;       // per task
   double2* d_ops = nullptr;
@@ -235,7 +252,11 @@ int max_bond(const pc_circuit* c) {
 
 void free_circuit(pc_circuit* c) {
   if (!c) return;
-  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_nrm); cudaFree(c->d_ops);
+  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_nrm);
+  cudaFree(c->d_X32); cudaFree(c->d_Q32); cudaFree(c->d_Qb); cudaFree(c->d_Y); cudaFree(c->d_jt32);
+  cudaFree(c->d_q64ptr); cudaFree(c->d_ns); cudaFree(c->d_xfro2); cudaFreeHost(c->h_xfro2);
+  cudaFreeHost(c->h_jtasks_y);
+  cudaFreeHost(c->h_jt32); cudaFreeHost(c->h_q64ptr); cudaFreeHost(c->h_ns); cudaFree(c->d_ops);
   cudaFree(c->d_tasks); cudaFree(c->d_jtasks); cudaFree(c->d_gemm); cudaFree(c->d_gemm2);
   cudaFree(c->d_split); cudaFree(c->d_jst); cudaFree(c->d_tout); cudaFree(c->d_idx);
   cudaFree(c->d_lamnew); cudaFree(c->d_sraw); cudaFree(c->d_bar); cudaFree(c->d_err); cudaFree(c->d_g2);
@@ -272,6 +293,21 @@ pc_status alloc_circuit(pc_circuit* c) {
   CUDA_TRY(ctx, cudaMalloc(&c->d_T0, (size_t)T * c->scratch_elems * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_Q, (size_t)T * c->scratch_elems * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_nrm, (size_t)T * 4 * X * sizeof(double)));
+  if (ctx->cfg.fp32_precondition) {
+    CUDA_TRY(ctx, cudaMalloc(&c->d_X32, (size_t)T * c->scratch_elems * sizeof(float2)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_Q32, (size_t)T * c->scratch_elems * sizeof(float2)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_Qb, (size_t)T * c->scratch_elems * sizeof(double2)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_Y, (size_t)T * c->scratch_elems * sizeof(double2)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_jt32, T * sizeof(pc::JacobiTask32)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_q64ptr, T * sizeof(double2*)));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_ns, 5 * T * sizeof(pc::GemmDesc)));
+    CUDA_TRY(ctx, cudaMallocHost(&c->h_jt32, T * sizeof(pc::JacobiTask32)));
+    CUDA_TRY(ctx, cudaMallocHost(&c->h_q64ptr, T * sizeof(double2*)));
+    CUDA_TRY(ctx, cudaMallocHost(&c->h_ns, 5 * T * sizeof(pc::GemmDesc)));
+    CUDA_TRY(ctx, cudaMallocHost(&c->h_jtasks_y, T * sizeof(pc::JacobiTask)));
+  }
+  CUDA_TRY(ctx, cudaMalloc(&c->d_xfro2, T * sizeof(double)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_xfro2, T * sizeof(double)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_ops, (size_t)T * 256 * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_tasks, T * sizeof(pc::UpdateTask)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_jtasks, T * sizeof(pc::JacobiTask)));
@@ -363,17 +399,22 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     g.A = u.Bl; g.B = u.Br; g.C = u.X; g.row_scale = nullptr;
     g.M = 4 * cl; g.N = 4 * cr; g.K = cm;
     g.lda = cm; g.ldb = 4 * cr; g.ldc = 4 * cr;
-    g.opB = 0; g.accumulate = 0; g.alpha = 1.0;
+    g.opB = 0; g.alpha = 1.0; g.beta = 0.0; g.D = nullptr;
     // The Jacobi orthogonalises min(m, n) vectors: the rows of X, or for a tall bond matrix
     // its columns, with the rotations accumulated into Q (the right singular vectors).
     pc::JacobiTask& jt = c->h_jtasks[t];
     jt.X = u.X;
     jt.Q = u.transposed ? c->d_Q + (size_t)t * c->scratch_elems : nullptr;
     jt.nrm2 = c->d_nrm + (size_t)t * 4 * c->chi_max;
+    jt.fro2 = c->d_xfro2 + t;
     jt.m = u.transposed ? u.n : u.m;
     jt.n = u.transposed ? u.m : u.n;
     jt.mp = jt.m + (jt.m & 1);
     jt.pad_ = 0;
+    {
+      const double r = ctx->cfg.eps / (10.0 * jt.m);
+      jt.dead_rel = r * r;
+    }
     max_m = std::max(max_m, u.m); max_n = std::max(max_n, u.n);
     max_len = std::max(max_len, jt.n);
     total_pairs += jt.mp / 2;
@@ -390,11 +431,9 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   timer_mark(c, 0);
   CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, T, max_m, max_n, s));
   CUDA_TRY(ctx, pc::launch_gate_apply(c->d_tasks, T, max_cl, max_cr, s));
-  CUDA_TRY(ctx, pc::launch_init_accumulators(c->d_jtasks, T, max_n, s));
   count_launch(c, 0, 2);
-  count_launch(c, 4, 1);
-  count_launch(c, 1, 1);
-  count_launch(c, 2, 1);
+  int max_vec = 0;
+  for (int t = 0; t < T; ++t) max_vec = std::max(max_vec, c->h_jtasks[t].m);
   for (int t = 0; t < T; ++t) {
     const pc::UpdateTask& u = c->h_tasks[t];
     c->t_flops[0] += 8.0 * u.m * (double)u.chi_m * u.n + 8.0 * 256.0 * u.chi_l * (double)u.chi_r;
@@ -402,25 +441,117 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     c->t_flops[1] += 4.0 * (4.0 * M * M * N + 22.0 * N * N * N);
   }
   timer_mark(c, 1);
-  CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
-                                  ctx->sm_count, max_len, total_pairs, s));
-  timer_mark(c, 2);
-  const int stride = 4 * c->chi_max;
-  CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,
-                                    c->d_sraw, stride, c->d_tout, s));
-  timer_mark(c, 3);
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_tout, c->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_jst, c->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  if (c->timing) {
-    float a = 0, b = 0, d = 0;
-    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
-    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
-    cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
-    c->t_ms[0] += a; c->t_ms[1] += b; c->t_ms[2] += d;
+  // Factorise every task of the wave: optionally FP32 preconditioning, then FP64 Jacobi
+  // sweeps, then truncation.  Returns with the outputs on the host.
+  // Which matrix holds each task's factorised rows once factorise() returns.
+  std::vector<double2*> final_x(T);
+  auto factorise = [&](bool precond) -> pc_status {
+    const size_t E = c->scratch_elems;
+    for (int t = 0; t < T; ++t) final_x[t] = c->h_jtasks[t].X;
+    // h_jtasks (X = the merged matrix, Q = the accumulator on the column path) is not
+    // modified after run_wave filled it
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
+    CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
+    CUDA_TRY(ctx, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+    CUDA_TRY(ctx, pc::launch_fro2(c->d_jtasks, T, c->d_xfro2, s));
+    count_launch(c, 1, 1);
+    if (!precond) {
+      CUDA_TRY(ctx, pc::launch_init_accumulators(c->d_jtasks, T, max_n, s));
+      count_launch(c, 4, 1);
+    } else {
+      // FP32 sweeps with the rotations accumulated in Q32; Q = polar(Q32) in FP64 by two
+      // Newton-Schulz steps Q <- 1.5 Q - 0.5 (Q Q^H) Q; X <- Q X; then the FP64 sweeps.
+      for (int t = 0; t < T; ++t) {
+        const pc::JacobiTask& jt = c->h_jtasks[t];
+        pc::JacobiTask32& j32 = c->h_jt32[t];
+        j32.X = c->d_X32 + (size_t)t * E;
+        j32.Q = c->d_Q32 + (size_t)t * E;
+        j32.nrm2 = reinterpret_cast<float*>(jt.nrm2);
+        j32.fro2 = jt.fro2;
+        j32.dead_rel = 1e-12 / jt.m;      // FP32 noise: a preconditioner may skip any pair
+        j32.m = jt.m; j32.n = jt.n; j32.mp = jt.mp; j32.pad_ = 0;
+        double2* QA = c->d_Q + (size_t)t * E;
+        double2* QB = c->d_Qb + (size_t)t * E;
+        double2* Y = c->d_Y + (size_t)t * E;
+        c->h_q64ptr[t] = QA;
+        const int v = jt.m, L = jt.n;
+        auto gd = [&](int stage) -> pc::GemmDesc& { return c->h_ns[stage * T + t]; };
+        for (int k = 0; k < 5; ++k) gd(k) = pc::GemmDesc{};
+        gd(0).A = QA; gd(0).lda = v; gd(0).B = QA; gd(0).ldb = v; gd(0).opB = 1; gd(0).C = Y; gd(0).ldc = v;
+        gd(0).M = v; gd(0).N = v; gd(0).K = v; gd(0).alpha = 1.0;
+        gd(1).A = Y; gd(1).lda = v; gd(1).B = QA; gd(1).ldb = v; gd(1).C = QB; gd(1).ldc = v; gd(1).D = QA;
+        gd(1).M = v; gd(1).N = v; gd(1).K = v; gd(1).alpha = -0.5; gd(1).beta = 1.5;
+        gd(2).A = QB; gd(2).lda = v; gd(2).B = QB; gd(2).ldb = v; gd(2).opB = 1; gd(2).C = Y; gd(2).ldc = v;
+        gd(2).M = v; gd(2).N = v; gd(2).K = v; gd(2).alpha = 1.0;
+        gd(3).A = Y; gd(3).lda = v; gd(3).B = QB; gd(3).ldb = v; gd(3).C = QA; gd(3).ldc = v; gd(3).D = QB;
+        gd(3).M = v; gd(3).N = v; gd(3).K = v; gd(3).alpha = -0.5; gd(3).beta = 1.5;
+        gd(4).A = QA; gd(4).lda = v; gd(4).B = jt.X; gd(4).ldb = L; gd(4).C = Y; gd(4).ldc = L;
+        gd(4).M = v; gd(4).N = L; gd(4).K = v; gd(4).alpha = 1.0;
+      }
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jt32, c->h_jt32, T * sizeof(pc::JacobiTask32), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_q64ptr, c->h_q64ptr, T * sizeof(double2*), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_ns, c->h_ns, 5 * T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(ctx, pc::launch_precond_init(c->d_jtasks, c->d_jt32, T, max_vec, max_len, s));
+      CUDA_TRY(ctx, pc::launch_jacobi32(c->d_jt32, T, c->d_jst, 40, c->d_bar, c->d_err, ctx->sm_count, max_len,
+                                        total_pairs, s));
+      CUDA_TRY(ctx, pc::launch_widen_q(c->d_jt32, c->d_q64ptr, T, max_vec, s));
+      for (int k = 0; k < 4; ++k) CUDA_TRY(ctx, pc::launch_gemm(c->d_ns + k * T, T, max_vec, max_vec, s));
+      CUDA_TRY(ctx, pc::launch_gemm(c->d_ns + 4 * T, T, max_vec, max_len, s));
+      count_launch(c, 1, 8);
+      // the FP64 sweeps run on Y = Q X, accumulating into Q on the column path
+      for (int t = 0; t < T; ++t) {
+        c->h_jtasks_y[t] = c->h_jtasks[t];
+        c->h_jtasks_y[t].X = c->d_Y + (size_t)t * E;
+        final_x[t] = c->h_jtasks_y[t].X;
+      }
+      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks_y, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
+      CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
+    }
+    CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
+                                    ctx->sm_count, max_len, total_pairs, s));
+    count_launch(c, 1, 1);
+    timer_mark(c, 2);
+    const int stride = 4 * c->chi_max;
+    CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,
+                                      c->d_sraw, stride, c->d_tout, s));
+    count_launch(c, 2, 1);
+    timer_mark(c, 3);
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_tout, c->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_jst, c->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_xfro2, c->d_xfro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (c->timing) {
+      float a = 0, b = 0, d = 0;
+      cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
+      cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+      cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+      c->t_ms[0] += a; c->t_ms[1] += b; c->t_ms[2] += d;
+    }
+    if (*c->h_err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+    return PC_OK;
+  };
+  const bool want_precond = ctx->cfg.fp32_precondition && max_vec >= 64;
+  pc_status fst = factorise(want_precond);
+  if (fst != PC_OK) return fst;
+  if (want_precond) {
+    // Safety net: Q X must keep the Frobenius norm of X (Q unitary).  Otherwise redo the
+    // wave in FP64 only.
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const double x2 = c->h_xfro2[t], y2 = c->h_tout[t].total2;
+      if (!(std::fabs(y2 - x2) <= 1e-9 * x2)) ok = false;
+    }
+    if (!ok) {
+      c->stats.fallbacks += 1;
+      timer_mark(c, 1);
+      fst = factorise(false);
+      if (fst != PC_OK) return fst;
+    }
   }
-  if (*c->h_err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+  const int stride = 4 * c->chi_max;
   for (int t = 0; t < T; ++t) {
     counts[t] = c->h_tout[t].count;
     c->stats.max_sweeps = std::max(c->stats.max_sweeps, c->h_jst[t].sweeps);
@@ -444,7 +575,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     const pc::UpdateTask& u = c->h_tasks[t];
     const int cnt = counts[t];
     pc::SplitRowsDesc& sd = c->h_split[nc];
-    sd.X = u.X;
+    sd.X = final_x[t];
     sd.Q = u.transposed ? c->h_jtasks[t].Q : nullptr;
     sd.dst = site_ptr(c, j + 1);
     sd.idx = c->d_idx + (size_t)t * stride;
@@ -455,7 +586,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
     g.A = u.T0; g.B = sd.dst; g.C = site_ptr(c, j); g.row_scale = nullptr;
     g.M = u.m; g.N = cnt; g.K = u.n;
     g.lda = u.n; g.ldb = u.n; g.ldc = cnt;
-    g.opB = 1; g.accumulate = 0; g.alpha = 1.0 / c->h_tout[t].nrm;
+    g.opB = 1; g.alpha = 1.0 / c->h_tout[t].nrm; g.beta = 0.0; g.D = nullptr;
     max_cnt = std::max(max_cnt, cnt); max_nn = std::max(max_nn, u.n); max_mm = std::max(max_mm, u.m);
     c->t_flops[3] += 8.0 * u.m * (double)u.n * cnt;
     ++nc;
@@ -735,11 +866,11 @@ pc_status project(pc_circuit* c) {
       g1.A = site_ptr(c, j) + 2 * sgm * cr; g1.lda = 4 * cr;
       g1.B = c->d_env + c->env_off[j + 1]; g1.ldb = cr;
       g1.C = tmp; g1.ldc = cr;
-      g1.M = cl; g1.N = cr; g1.K = cr; g1.opB = 0; g1.accumulate = 0; g1.alpha = 1.0;
+      g1.M = cl; g1.N = cr; g1.K = cr; g1.opB = 0; g1.alpha = 1.0; g1.beta = 0.0;
       g2.A = tmp; g2.lda = cr;
       g2.B = site_ptr(c, j) + 2 * sgm * cr; g2.ldb = 4 * cr;
       g2.C = c->d_env + c->env_off[j]; g2.ldc = cl;
-      g2.M = cl; g2.N = cl; g2.K = cr; g2.opB = 1; g2.accumulate = sgm; g2.alpha = 1.0;
+      g2.M = cl; g2.N = cl; g2.K = cr; g2.opB = 1; g2.alpha = 1.0; g2.beta = sgm;
       c->h_gemm[0] = g1;
       CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cr, c->stream));
@@ -780,6 +911,7 @@ void pc_default_config(pc_config* cfg) {
   cfg->unswap_mode = PC_UNSWAP_PARALLEL;
   cfg->jacobi_max_sweeps = 60;
   cfg->device = 0;
+  cfg->fp32_precondition = 1;
 }
 
 pc_status pc_create(const pc_config* cfg, pc_ctx** out) {

@@ -6,7 +6,8 @@
 
 namespace pc {
 
-// One complex FP64 GEMM of a batch: C = alpha * A * op(B) (+ C if accumulate).
+// One complex FP64 GEMM of a batch: C = alpha * A * op(B) + beta * D, where D is the
+// matrix D (same leading dimension as C) or, when D is null, C itself.
 //   A  : M x K row-major, leading dimension lda (complex elements)
 //   B  : op == 0: K x N row-major (ldb);  op == 1: N x K row-major (ldb), used as its
 //        conjugate transpose
@@ -20,8 +21,10 @@ struct GemmDesc {
   int32_t M, N, K;
   int32_t lda, ldb, ldc;
   int32_t opB;          // 0: B, 1: B^H
-  int32_t accumulate;   // 0: C = ..., 1: C += ...
+  int32_t pad_;
   double alpha;
+  double beta;          // 0: C is only written
+  const double2* D;     // addend (nullptr: C)
 };
 
 // One two-site update of a wave (Sec. II.B.1): sites (j, j+1) with bond dims
@@ -44,12 +47,29 @@ struct UpdateTask {
 // tall bond matrix), because more vectors than dimensions cannot all be made orthogonal.
 // When Q is given (m x m, set to the identity), every rotation is also applied to the rows
 // of Q, which then holds the accumulated unitary.
+// Pairs of rows that are both below the noise floor dead2 = dead_rel * |X|_F^2 are not
+// rotated (nullptr fro2: no floor).  Any pair with a row above the floor is, so the kept
+// rows end orthogonal to everything; rows below the floor stay below the cutoff whatever
+// they combine to when dead_rel <= (eps_cut / (10 m))^2.
 struct JacobiTask {
   double2* X;             // m x n row-major; rows are orthogonalised in place
   double2* Q;             // optional m x m accumulator (nullptr: none)
   double* nrm2;           // m squared row norms (scratch owned by the kernel)
+  const double* fro2;     // squared Frobenius norm of X (or nullptr)
+  double dead_rel;
   int32_t m, n;
   int32_t mp;             // m rounded up to even
+  int32_t pad_;
+};
+// The same for the FP32 preconditioning sweeps (single-precision complex).
+struct JacobiTask32 {
+  float2* X;
+  float2* Q;
+  float* nrm2;
+  const double* fro2;
+  double dead_rel;
+  int32_t m, n;
+  int32_t mp;
   int32_t pad_;
 };
 struct JacobiStatus {
@@ -67,12 +87,24 @@ struct TruncOut {
   double s0;              // largest singular value
   double nrm;             // sqrt(sum of kept s^2)
   double s_first_dropped; // first singular value not kept (0 if none)
+  double total2;          // sum of the squares of all row norms (= squared Frobenius norm)
 };
 
 // Launch wrappers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_gemm(const GemmDesc* d_desc, int batch, int max_m, int max_n, cudaStream_t stream);
 cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi_l, int max_chi_r,
                               cudaStream_t stream);
+// FP32 preconditioning: X32 = float(X) and Q32 = I for every task (dims from the FP64 task).
+cudaError_t launch_precond_init(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m,
+                                int max_n, cudaStream_t stream);
+// Squared Frobenius norm of each task's FP64 matrix into d_out[t].
+cudaError_t launch_fro2(const JacobiTask* d_t64, int ntasks, double* d_out, cudaStream_t stream);
+// Q64 = double(Q32) for every task (m x m).
+cudaError_t launch_widen_q(const JacobiTask32* d_t32, double2* const* d_q64, int ntasks, int max_m,
+                           cudaStream_t stream);
+cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                            unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
+                            cudaStream_t stream);
 // Sets every task's accumulator Q (if any) to the identity.
 cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 // Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the
