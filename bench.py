@@ -143,6 +143,70 @@ def oracle_sample(seed: int, budget_s: float, min_updates: int = 2):
     return done, dt
 
 
+MIX_KW = dict(eps=1e-10, chi_max=64, tau=3000)
+MIX_COUNT = 8
+
+
+def measure_batching(binding):
+    """The same mix of independent circuits contracted one after another (each on its own
+    workspace) and as one batch (pc_batch_contract: every factorisation of every circuit in
+    shared launches).  Wall time of each, launches, tasks per launch."""
+    circs = W.circuit_mix(MIX_COUNT, seed=0)
+    ctx = binding.Context(**MIX_KW)
+    t0 = time.perf_counter()
+    waves = 0
+    for circ in circs:
+        c = ctx.load_circuit(circ)
+        waves += c.contract()["n_waves"]
+        c.extract_peak()
+        c.close()
+    t_seq = time.perf_counter() - t0
+    hs = [ctx.load_circuit(circ) for circ in circs]
+    batch = binding.Batch(ctx, max_tasks=256)
+    t0 = time.perf_counter()
+    batch.contract(hs)
+    for h in hs:
+        h.extract_peak()
+    t_bat = time.perf_counter() - t0
+    cnt = batch.counters()
+    for h in hs:
+        h.close()
+    batch.close()
+    ctx.close()
+    return {"workload": f"{MIX_COUNT} hidden-permutation mirrors, n in [8,12], 12-24 Haar gates/half, "
+                        f"perturbation in [0,0.04], chi_max=64, eps=1e-10, tau=3000",
+            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
+            "sequential_waves": waves, "batched_launches": cnt["launches"],
+            "tasks_per_launch": cnt["tasks"] / max(cnt["launches"], 1), "max_tasks_per_launch": cnt["max_tasks"]}
+
+
+def measure_serving(binding, precision: int, rate: float, count: int = 16):
+    """A Poisson stream of `count` requests (the circuit mix above, cutoff 1e-5 so both
+    precisions reach the same bond dimensions) through pc_server: p50/p99 time-to-peak and
+    circuits/hour."""
+    circs = W.circuit_mix(count, seed=1)
+    arrivals = W.poisson_arrivals(count, rate, seed=precision)
+    srv = binding.Server(max_resident=8, memory_budget=16 << 30, max_tasks=256)
+    t0 = time.perf_counter()
+    tickets = []
+    for circ, ta in zip(circs, arrivals):
+        delay = ta - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(circ, n_samples=100, seed=5, eps=1e-5, chi_max=64, tau=3000,
+                                  precision=precision))
+    ok = 0
+    for t in tickets:
+        res, _, _ = srv.wait(t, timeout_s=600)
+        ok += res["status"] == 0
+    st = srv.stats()
+    srv.close()
+    return {"precision": ["fp64", "tf32x3 merges"][precision], "requests": count, "rate_per_s": rate,
+            "completed": ok, "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+            "circuits_per_hour": st["circuits_per_hour"], "max_resident": st["max_resident_seen"],
+            "launches": st["launches"], "tasks_per_launch": st["tasks"] / max(st["launches"], 1)}
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
@@ -273,6 +337,8 @@ def run_ours(args):
                        "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write); "
                        "working set > L2"},
             "time_to_peak_ms_per_step": t_max / args.steps,
+            "jacobi_sweeps": {"fp64_max": stats["max_sweeps"], "fp32_max": stats["max_sweeps_fp32"],
+                              "fallbacks": stats["fallbacks"]},
             "peak_probability": p,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -287,6 +353,13 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
         }
+        if world == 1 and not args.no_serving:
+            line["batching"] = measure_batching(binding)
+            cap = MIX_COUNT / line["batching"]["batched_s"]        # circuits/s the batch sustains
+            line["serving"] = {"workload": "Poisson arrivals at 0.5x the batched capacity of the mix above; "
+                                           "16 requests, 100 samples each, eps=1e-5, chi_max=64",
+                               "fp64": measure_serving(binding, 0, 0.5 * cap),
+                               "mixed": measure_serving(binding, 1, 0.5 * cap)}
         print(json.dumps(line), flush=True)
     c.close()
     ctx.close()
@@ -301,6 +374,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batching and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

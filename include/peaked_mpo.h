@@ -53,6 +53,10 @@ typedef int32_t pc_status;
 #define PC_UNSWAP_SEQUENTIAL 1    /* Algorithm 1: largest available bond, one at a time  */
 #define PC_UNSWAP_OFF        2    /* no unswapping (the plain Middle-MPO attack, Sec. I) */
 
+#define PC_PRECISION_FP64    0    /* every step in FP64                                   */
+#define PC_PRECISION_TF32X3  1    /* merges as complex 3xTF32 on tcgen05 tensor cores with */
+                                  /* FP32 accumulation; factorisation and truncation FP64  */
+
 #define PC_SIDE_LEFT  0           /* out-legs: M <- g M   */
 #define PC_SIDE_RIGHT 1           /* in-legs:  M <- M h   */
 #define PC_SIDE_BOTH  2
@@ -74,6 +78,7 @@ typedef struct pc_config {
                              /* sweeps; the accumulated rotation is made unitary in FP64   */
                              /* (two Newton-Schulz steps) and applied, then FP64 sweeps    */
                              /* finish.  The result keeps FP64 accuracy.  0: FP64 only.     */
+  int32_t precision;         /* PC_PRECISION_*: arithmetic of the two-site merge          */
 } pc_config;
 
 /* Counters filled by pc_contract. */
@@ -90,6 +95,7 @@ typedef struct pc_stats {
   int32_t fallbacks;         /* waves redone in FP64 only after a failed norm check of   */
                              /* the FP32 preconditioning                                  */
   double seconds;            /* host wall time of the call                                */
+  int32_t max_sweeps_fp32;   /* largest FP32 preconditioning sweep count of one update     */
 } pc_stats;
 
 /* Fills cfg with the paper's defaults except eps/chi_max (1e-10 / 256) and tau (1e6). */
@@ -224,6 +230,109 @@ pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
  * make it before any stream capture. */
 pc_status pc_factorise_noalloc(const double* x_dev, int32_t m, int32_t n, double eps, int32_t chi_max,
                                double* s_dev, double* vh_dev, int32_t* count, void* stream);
+
+/* ---- Batching: the waves of several circuits in one set of launches -------------------
+ * A batch owns a launcher thread and one factorisation workspace.  A circuit attached to a
+ * batch posts each of its waves (absorption updates, unswap trials) to the launcher instead
+ * of launching them itself; the launcher combines the waves posted by every attached
+ * circuit that is contracting into launches of at most max_tasks factorisations of any mix
+ * of bond dimensions, precisions and configurations (one persistent Jacobi launch for all),
+ * waiting at most about 2 ms for a circuit that has not posted yet.  Results per circuit
+ * are the ones it gets alone, up to the rounding order of the shared launch (the Jacobi
+ * group width depends on the launch's total work).  The paper runs one circuit at a time
+ * (Sec. III); this is the library's own scheduling. */
+typedef struct pc_batch pc_batch;
+
+/* A batch on ctx's device: max_tasks factorisations per launch (1..256), scratch arena of at
+ * most arena_bytes (0: 8 GiB), allocated as needed.  Destroy it only after every circuit
+ * has been detached. */
+pc_status pc_batch_create(pc_ctx* ctx, int32_t max_tasks, int64_t arena_bytes, pc_batch** out);
+pc_status pc_batch_destroy(pc_batch* b);
+/* Routes c's waves through the batch (attach) or back to the circuit's own workspace. */
+pc_status pc_batch_attach(pc_batch* b, pc_circuit* c);
+pc_status pc_batch_detach(pc_batch* b, pc_circuit* c);
+/* pc_contract on n distinct circuits at once, one host thread each, their waves combined.
+ * statuses[k] receives circuit k's status, stats[k] (stats may be NULL) its counters.
+ * Returns the most recent error status among them, else PC_OK. */
+pc_status pc_batch_contract(pc_batch* b, int32_t n, pc_circuit* const* circuits, pc_status* statuses,
+                            pc_stats* stats);
+/* Combined launches so far, factorisations they ran, the largest launch, and per kernel
+ * class (as pc_kernel_timers) the milliseconds (when timing is on) and algorithmic flops. */
+pc_status pc_batch_counters(pc_batch* b, int64_t* launches, int64_t* tasks, int32_t* max_tasks, double* ms,
+                            double* flops);
+pc_status pc_batch_set_timing(pc_batch* b, int32_t enable);
+
+/* Device bytes a circuit of n_qubits at chi_max keeps resident while served: site store,
+ * spectra, right environments, peak-search pool and the buffers of n_samples samples.
+ * Host-only.  -1 for invalid sizes. */
+int64_t pc_projected_bytes(int32_t n_qubits, int32_t chi_max, int64_t n_samples);
+
+/* ---- Serving: a request loop with continuous batching ----------------------------------
+ * Requests (a circuit and its configuration) may be submitted at any time.  The server
+ * admits them in arrival order as soon as a slot is free and the circuit's projected bytes
+ * (pc_projected_bytes at its chi_max) fit in memory_budget next to the resident ones; each
+ * admitted circuit stays resident until its peak (and samples) are ready, and the
+ * factorisations of all contracting circuits run in shared launches of one batch.
+ * Time-to-peak of a request = completion - submission on the server clock. */
+typedef struct pc_server pc_server;
+
+typedef struct pc_server_config {
+  int32_t device;
+  int32_t max_resident;      /* circuits admitted at once (slots), >= 1                     */
+  int64_t memory_budget;     /* bytes for the resident circuits' stores, > 0                */
+  int32_t max_tasks;         /* factorisations per combined launch, 1..256                  */
+  int64_t arena_bytes;       /* shared factorisation scratch (0: 8 GiB), besides the budget */
+} pc_server_config;
+
+typedef struct pc_request {
+  pc_config cfg;             /* eps, chi_max, tau, precision, ...; cfg.device is ignored     */
+  int32_t n_qubits;
+  int64_t n_gates;
+  const int32_t* pairs;      /* as pc_load_gates; copied by pc_server_submit                */
+  const double* mats;
+  int64_t split_index;
+  int64_t n_oneq;
+  const int32_t* oneq_qubits;
+  const double* oneq_mats;
+  int64_t n_samples;         /* samples to draw from the result (0: none), as pc_sample     */
+  uint64_t seed;
+} pc_request;
+
+typedef struct pc_result {
+  pc_status status;          /* of the request's contraction, peak and sampling            */
+  int32_t n_qubits;
+  double p_peak;             /* as pc_extract_peak                                          */
+  double norm2;
+  double t_submit, t_admit, t_done;   /* seconds on the server clock                       */
+  int64_t n_updates, n_trials, n_accepted;
+  int32_t max_chi;
+  int64_t store_bytes;       /* projected bytes it held while resident                      */
+} pc_result;
+
+typedef struct pc_server_stats {
+  int64_t submitted, admitted, completed, failed;
+  int32_t resident, max_resident_seen;
+  int64_t bytes_resident, max_bytes_seen;
+  double p50_s, p99_s, mean_s;   /* time-to-peak of the completed requests (nearest rank)   */
+  double circuits_per_hour;      /* completed / (last completion - first submission)        */
+  int64_t launches, tasks;       /* combined factorisation launches and their tasks         */
+  int32_t max_tasks_per_launch;
+} pc_server_stats;
+
+pc_status pc_server_create(const pc_server_config* cfg, pc_server** out);
+/* Copies the request; *ticket identifies it.  A request whose projected bytes exceed
+ * memory_budget completes with PC_ERR_OOM without being admitted. */
+pc_status pc_server_submit(pc_server* s, const pc_request* req, int64_t* ticket);
+/* Waits for a request (timeout_s < 0: without limit; PC_ERR_TIMEOUT when it is not done in
+ * time) and copies its result: bits uint8[n] (the peak, may be NULL), samples
+ * uint8[n_samples][n] (may be NULL). */
+pc_status pc_server_wait(pc_server* s, int64_t ticket, double timeout_s, pc_result* res, uint8_t* bits,
+                         uint8_t* samples);
+pc_status pc_server_get_stats(pc_server* s, pc_server_stats* out);
+/* Seconds since pc_server_create. */
+double pc_server_clock(pc_server* s);
+/* Finishes every submitted request, then frees the server. */
+pc_status pc_server_destroy(pc_server* s);
 
 /* The CUDA stream (a cudaStream_t) every kernel of this circuit runs on, for callers that
  * time or order their own work against it.  The circuit keeps ownership. */

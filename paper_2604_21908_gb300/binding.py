@@ -19,22 +19,57 @@ STATUS_NAMES = {0: "PC_OK", -1: "PC_ERR_INVALID_ARG", -2: "PC_ERR_NONUNITARY", -
                 -4: "PC_ERR_NOCONVERGE", -5: "PC_ERR_TIMEOUT", -6: "PC_ERR_NOT_PEAKED", -7: "PC_ERR_CUDA",
                 -8: "PC_ERR_STATE", 1: "PC_WARN_STALLED"}
 UNSWAP_PARALLEL, UNSWAP_SEQUENTIAL, UNSWAP_OFF = 0, 1, 2
+PRECISION_FP64, PRECISION_TF32X3 = 0, 1
 
 
 class PcConfig(C.Structure):
     _fields_ = [("eps", C.c_double), ("chi_max", C.c_int32), ("tau", C.c_double),
                 ("max_unswap_iter", C.c_int32), ("accept_equal", C.c_int32), ("unswap_mode", C.c_int32),
-                ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32), ("fp32_precondition", C.c_int32)]
+                ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32), ("fp32_precondition", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class PcStats(C.Structure):
     _fields_ = [("n_updates", C.c_int64), ("n_trials", C.c_int64), ("n_accepted", C.c_int64),
                 ("n_stages", C.c_int64), ("n_waves", C.c_int64), ("final_size", C.c_int64),
                 ("max_chi", C.c_int32), ("stalled", C.c_int32), ("max_sweeps", C.c_int32), ("fallbacks", C.c_int32),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("max_sweeps_fp32", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
+
+
+class PcServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_resident", C.c_int32), ("memory_budget", C.c_int64),
+                ("max_tasks", C.c_int32), ("arena_bytes", C.c_int64)]
+
+
+class PcRequest(C.Structure):
+    _fields_ = [("cfg", PcConfig), ("n_qubits", C.c_int32), ("n_gates", C.c_int64), ("pairs", C.c_void_p),
+                ("mats", C.c_void_p), ("split_index", C.c_int64), ("n_oneq", C.c_int64),
+                ("oneq_qubits", C.c_void_p), ("oneq_mats", C.c_void_p), ("n_samples", C.c_int64),
+                ("seed", C.c_uint64)]
+
+
+class PcResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_qubits", C.c_int32), ("p_peak", C.c_double), ("norm2", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("n_updates", C.c_int64), ("n_trials", C.c_int64), ("n_accepted", C.c_int64),
+                ("max_chi", C.c_int32), ("store_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PcServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("resident", C.c_int32), ("max_resident_seen", C.c_int32), ("bytes_resident", C.c_int64),
+                ("max_bytes_seen", C.c_int64), ("p50_s", C.c_double), ("p99_s", C.c_double), ("mean_s", C.c_double),
+                ("circuits_per_hour", C.c_double), ("launches", C.c_int64), ("tasks", C.c_int64),
+                ("max_tasks_per_launch", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class PcError(RuntimeError):
@@ -50,7 +85,10 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_get_bond_dims", "pc_get_layouts", "pc_get_spectrum", "pc_get_site", "pc_set_state",
            "pc_apply_updates", "pc_plan_routing", "pc_get_plan", "pc_get_unswap_log", "pc_kernel_timers",
            "pc_reset_kernel_timers", "pc_contract_iterations", "pc_get_cursors", "pc_set_cursors", "pc_snapshot",
-           "pc_restore", "pc_get_stream", "pc_factorise_noalloc"]
+           "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_batch_create", "pc_batch_destroy",
+           "pc_batch_attach", "pc_batch_detach", "pc_batch_contract", "pc_batch_counters", "pc_batch_set_timing",
+           "pc_projected_bytes", "pc_server_create", "pc_server_submit", "pc_server_wait", "pc_server_get_stats",
+           "pc_server_clock", "pc_server_destroy"]
 
 
 def _p(t):
@@ -99,6 +137,20 @@ def load(path: str = LIB_PATH):
         "pc_get_stream": ([vp, _p(vp)], i32),
         "pc_factorise_noalloc": ([vp, i32, i32, dbl, i32, vp, vp, _p(i32), vp], i32),
         "pc_reset_kernel_timers": ([vp, i32], i32),
+        "pc_batch_create": ([vp, i32, i64, _p(vp)], i32),
+        "pc_batch_destroy": ([vp], i32),
+        "pc_batch_attach": ([vp, vp], i32),
+        "pc_batch_detach": ([vp, vp], i32),
+        "pc_batch_contract": ([vp, i32, vp, vp, vp], i32),
+        "pc_batch_counters": ([vp, _p(i64), _p(i64), _p(i32), vp, vp], i32),
+        "pc_batch_set_timing": ([vp, i32], i32),
+        "pc_projected_bytes": ([i32, i32, i64], i64),
+        "pc_server_create": ([_p(PcServerConfig), _p(vp)], i32),
+        "pc_server_submit": ([vp, _p(PcRequest), _p(i64)], i32),
+        "pc_server_wait": ([vp, i64, dbl, _p(PcResult), vp, vp], i32),
+        "pc_server_get_stats": ([vp, _p(PcServerStats)], i32),
+        "pc_server_clock": ([vp], dbl),
+        "pc_server_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -340,6 +392,139 @@ class Circuit:
     def close(self):
         if self.h:
             self.lib.pc_destroy_circuit(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def projected_bytes(n_qubits: int, chi_max: int, n_samples: int = 0) -> int:
+    """pc_projected_bytes: device bytes a served circuit keeps resident (host-only)."""
+    return int(load().pc_projected_bytes(n_qubits, chi_max, n_samples))
+
+
+def _gate_arrays(circ):
+    pairs = np.ascontiguousarray(circ.pairs, dtype=np.int32).reshape(-1, 2)
+    mats = np.asarray(circ.mats)
+    if np.iscomplexobj(mats):
+        mats = np.stack([mats.real, mats.imag], axis=-1)
+    mats = np.ascontiguousarray(mats, dtype=np.float64).reshape(-1, 4, 4, 2)
+    if circ.oneq_qubits is None or len(circ.oneq_qubits) == 0:
+        oq = np.zeros(0, np.int32)
+        om = np.zeros((0, 2, 2, 2))
+    else:
+        oq = np.ascontiguousarray(circ.oneq_qubits, dtype=np.int32)
+        om = np.asarray(circ.oneq_mats)
+        if np.iscomplexobj(om):
+            om = np.stack([om.real, om.imag], axis=-1)
+        om = np.ascontiguousarray(om, dtype=np.float64)
+    return pairs, mats, oq, om
+
+
+class Batch:
+    """pc_batch_*: combined launches of the waves of several circuits."""
+
+    def __init__(self, ctx: Context, max_tasks: int = 256, arena_bytes: int = 0):
+        self.ctx, self.lib = ctx, ctx.lib
+        h = C.c_void_p()
+        ctx.check(self.lib.pc_batch_create(ctx.h, max_tasks, arena_bytes, C.byref(h)), "pc_batch_create")
+        self.h = h
+
+    def contract(self, circuits):
+        """pc_batch_contract: returns (statuses, list of stats dicts)."""
+        n = len(circuits)
+        handles = (C.c_void_p * n)(*[c.h for c in circuits])
+        statuses = np.zeros(n, dtype=np.int32)
+        stats = (PcStats * n)()
+        st = self.lib.pc_batch_contract(self.h, n, C.cast(handles, C.c_void_p), _ptr(statuses),
+                                        C.cast(stats, C.c_void_p))
+        for k, c in enumerate(circuits):
+            if statuses[k] < 0:
+                c._chk(int(statuses[k]), "pc_batch_contract")
+        if st < 0:
+            raise PcError(st, "pc_batch_contract")
+        return statuses, [s.as_dict() for s in stats]
+
+    def counters(self):
+        la, ta = C.c_int64(0), C.c_int64(0)
+        mt = C.c_int32(0)
+        ms = np.zeros(5)
+        fl = np.zeros(5)
+        self.lib.pc_batch_counters(self.h, C.byref(la), C.byref(ta), C.byref(mt), _ptr(ms), _ptr(fl))
+        return {"launches": la.value, "tasks": ta.value, "max_tasks": mt.value, "ms": ms, "flops": fl}
+
+    def set_timing(self, enable=True):
+        self.lib.pc_batch_set_timing(self.h, 1 if enable else 0)
+
+    def close(self):
+        if self.h:
+            self.lib.pc_batch_destroy(self.h)
+            self.h = None
+
+
+class Server:
+    """pc_server_*: request loop with admission by projected device memory and continuous
+    batching of every resident circuit's factorisations."""
+
+    def __init__(self, max_resident=8, memory_budget=64 << 30, max_tasks=256, arena_bytes=0, device=0):
+        self.lib = load()
+        cfg = PcServerConfig(device, max_resident, memory_budget, max_tasks, arena_bytes)
+        h = C.c_void_p()
+        st = self.lib.pc_server_create(C.byref(cfg), C.byref(h))
+        if st != PC_OK:
+            raise PcError(st, "pc_server_create")
+        self.h = h
+        self.n_of = {}
+        self.samples_of = {}
+
+    def submit(self, circ, n_samples=0, seed=0, **cfg_kw) -> int:
+        pairs, mats, oq, om = _gate_arrays(circ)
+        req = PcRequest()
+        req.cfg = default_config(**cfg_kw)
+        req.n_qubits = circ.n_qubits
+        req.n_gates = pairs.shape[0]
+        req.pairs = pairs.ctypes.data
+        req.mats = mats.ctypes.data
+        req.split_index = circ.split_index
+        req.n_oneq = oq.shape[0]
+        req.oneq_qubits = oq.ctypes.data
+        req.oneq_mats = om.ctypes.data
+        req.n_samples = n_samples
+        req.seed = seed
+        t = C.c_int64(0)
+        st = self.lib.pc_server_submit(self.h, C.byref(req), C.byref(t))
+        if st != PC_OK:
+            raise PcError(st, "pc_server_submit")
+        self.n_of[t.value] = circ.n_qubits
+        self.samples_of[t.value] = n_samples
+        return t.value
+
+    def wait(self, ticket, timeout_s=-1.0):
+        """(result dict, peak bits, samples or None)."""
+        n, S = self.n_of[ticket], self.samples_of[ticket]
+        res = PcResult()
+        bits = np.zeros(n, dtype=np.uint8)
+        samples = np.zeros((S, n), dtype=np.uint8) if S > 0 else None
+        st = self.lib.pc_server_wait(self.h, ticket, timeout_s, C.byref(res), _ptr(bits),
+                                     _ptr(samples) if samples is not None else None)
+        if st != PC_OK:
+            raise PcError(st, "pc_server_wait")
+        return res.as_dict(), bits, samples
+
+    def stats(self) -> dict:
+        out = PcServerStats()
+        self.lib.pc_server_get_stats(self.h, C.byref(out))
+        return out.as_dict()
+
+    def clock(self) -> float:
+        return float(self.lib.pc_server_clock(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.pc_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_NAME = "libpeaked_mpo.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
-SOURCES = ["kernels.cu", "pc_api.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "pc_api.cpp", "noalloc.cu", "merge_tc.cu", "pc_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -192,6 +192,14 @@ template <> struct JacTraits<double> {
   static constexpr double tiny = 1e-280;                   // floor for squared row norms
   static constexpr double g2min = 1e-290;                  // |g|^2 below this is not rotated
   static constexpr double huge = 1e100;
+  // Carried squared norms are recomputed exactly (a) when the two of a pair differ by more
+  // than `recompute` (each rotation moves a carried value by roundoff of the larger norm),
+  // (b) when they agree to `degenerate` (the rotation angle depends on their difference,
+  // which carried roundoff would swamp), (c) when an update cancelled below `cancel` of the
+  // old value (marked by a negative carried value).
+  static constexpr double recompute = 1e-8;
+  static constexpr double degenerate = 1e-8;
+  static constexpr double cancel = 1e-3;
 };
 template <> struct JacTraits<float> {
   using C = float2;
@@ -203,6 +211,9 @@ template <> struct JacTraits<float> {
   static constexpr float tiny = 1e-30f;
   static constexpr float g2min = 1e-36f;
   static constexpr float huge = 1e18f;
+  static constexpr float recompute = 1e-3f;
+  static constexpr float degenerate = 1e-3f;
+  static constexpr float cancel = 0.1f;
 };
 
 __device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
@@ -270,10 +281,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
   __shared__ R s_red[2][NG][G][4];
   __shared__ R s_rot[NG][8];
   __shared__ R s_dead2[JAC_MAX_TASKS];
+  __shared__ R s_marg2[JAC_MAX_TASKS];
   for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
     s_done[t] = 0;
     s_task[t] = tasks[t];
     s_dead2[t] = s_task[t].fro2 ? (R)(s_task[t].dead_rel * *s_task[t].fro2) : R(0);
+    s_marg2[t] = R(6 * s_task[t].m) * s_dead2[t];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -347,7 +360,13 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
       const int n = tk.n;
       // the carried norms, fetched early so their latency overlaps the row loads
       R na_pre = R(0), nb_pre = R(0);
-      if (!full && (G == 1 || gl < 32)) { na_pre = tk.nrm2[a]; nb_pre = tk.nrm2[b]; }
+      bool exact = full;
+      if (!full) {
+        na_pre = tk.nrm2[a];
+        nb_pre = tk.nrm2[b];
+        exact = !(fmin(na_pre, nb_pre) > JacTraits<R>::recompute * fmax(na_pre, nb_pre)) ||
+                fabs(na_pre - nb_pre) < JacTraits<R>::degenerate * (na_pre + nb_pre);
+      }
       const bool in_regs = n <= GT * JAC_E;
       C ra[JAC_E], rb[JAC_E];
       R aa = R(0), bb = R(0), gr = R(0), gi = R(0);
@@ -363,7 +382,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
           const C u = ra[e], v = rb[e];
           gr = fma(u.x, v.x, fma(u.y, v.y, gr));
           gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
-          if (full) {
+          if (exact) {
             aa = fma(u.x, u.x, fma(u.y, u.y, aa));
             bb = fma(v.x, v.x, fma(v.y, v.y, bb));
           }
@@ -373,7 +392,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
           const C u = xa[k], v = xb[k];
           gr = fma(u.x, v.x, fma(u.y, v.y, gr));
           gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
-          if (full) {
+          if (exact) {
             aa = fma(u.x, u.x, fma(u.y, u.y, aa));
             bb = fma(v.x, v.x, fma(v.y, v.y, bb));
           }
@@ -390,12 +409,19 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
       R tg = R(0);                            // t |g|, for the norm update
       int rotate;
       if (G == 1 || gl < 32) {
-        if (!full) { aa = na_pre; bb = nb_pre; }
+        if (!exact) { aa = na_pre; bb = nb_pre; }
         const R g2 = fma(gr, gr, gi * gi);
         const R tol = R(2) * eps * sqrt(R(n));
         // rows at the underflow floor are zero for every purpose here
-        const R dead2 = s_dead2[t];
-        rotate = !(aa < JacTraits<R>::tiny || bb < JacTraits<R>::tiny) && !(aa < dead2 && bb < dead2) &&
+        // Floors: no pair of two rows below dead2, and no pair of a row below dead2 with a row
+        // below marg2 = 6 m dead2, is rotated.  The rows below marg2 stay below the cutoff and
+        // are orthogonalised among themselves and against every row above marg2; the rows
+        // above marg2 against everything.  Without the second floor a row just above dead2
+        // keeps re-mixing the (mutually non-orthogonal) rows below it and converges linearly.
+        const R dead2 = s_dead2[t], marg2 = s_marg2[t];
+        const R lo2 = fmin(aa, bb), hi2 = fmax(aa, bb);
+        rotate = !(aa < JacTraits<R>::tiny || bb < JacTraits<R>::tiny) && !(hi2 < dead2) &&
+                 !(lo2 < dead2 && hi2 < marg2) &&
                  g2 >= JacTraits<R>::g2min && (g2 > (tol * tol) * aa * bb);
         if (rotate) {
           const R gabs = sqrt(g2);
@@ -432,7 +458,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         // of the group reaches only after reading these values
       }
       if (!rotate) {
-        if (full && gl == 0) { tk.nrm2[a] = aa; tk.nrm2[b] = bb; }
+        if (exact && gl == 0) { tk.nrm2[a] = aa; tk.nrm2[b] = bb; }
         continue;
       }
       if (in_regs) {
@@ -464,8 +490,11 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         }
       }
       if (gl == 0) {
-        tk.nrm2[a] = aa - tg;
-        tk.nrm2[b] = bb + tg;
+        R na = aa - tg, nb = bb + tg;
+        if (na < JacTraits<R>::cancel * aa) na = -na;
+        if (nb < JacTraits<R>::cancel * bb) nb = -nb;
+        tk.nrm2[a] = na;
+        tk.nrm2[b] = nb;
         atomicAdd(&st[t].rot[s % 3], 1u);
       }
     }
@@ -519,17 +548,16 @@ __global__ void widen_q_kernel(const JacobiTask32* __restrict__ t32, double2* co
 // chi_max) and renormalise the kept values to unit 2-norm.
 constexpr int TR_MAX = 4096;
 
-__global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __restrict__ tasks,
-                                                        double eps, int chi_max, int32_t* idx_out,
-                                                        int idx_stride, double* lam_out,
-                                                        double* sraw_out, int lam_stride,
-                                                        TruncOut* out) {
+// One CTA truncates the m rows of X (length n) of one task; outputs at idx_out, lam_out,
+// sraw_out (count entries each) and *out.
+__device__ void truncate_body(const double2* X, int m, int n, double eps, int chi_max, int32_t* idx_out,
+                              double* lam_out, double* sraw_out, TruncOut* out) {
   extern __shared__ unsigned char smem_raw[];
   double* sv = reinterpret_cast<double*>(smem_raw);
   int* id = reinterpret_cast<int*>(sv + TR_MAX);
   __shared__ double red[32];
   __shared__ int s_count;
-  const JacobiTask t = tasks[blockIdx.x];
+  struct { const double2* X; int m, n; } t{X, m, n};
   int P = 1;
   while (P < t.m) P <<= 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -598,9 +626,9 @@ __global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __rest
   }
   __syncthreads();
   for (int k = threadIdx.x; k < count; k += blockDim.x) {
-    idx_out[(size_t)blockIdx.x * idx_stride + k] = id[k];
-    lam_out[(size_t)blockIdx.x * lam_stride + k] = sv[k] / nrm;
-    sraw_out[(size_t)blockIdx.x * lam_stride + k] = sv[k];
+    idx_out[k] = id[k];
+    lam_out[k] = sv[k] / nrm;
+    sraw_out[k] = sv[k];
   }
   if (threadIdx.x == 0) {
     TruncOut o;
@@ -610,8 +638,23 @@ __global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __rest
     o.nrm = nrm;
     o.s_first_dropped = count < t.m ? sv[count] : 0.0;
     o.total2 = red[1];
-    out[blockIdx.x] = o;
+    *out = o;
   }
+}
+
+__global__ void __launch_bounds__(1024) truncate_kernel(const JacobiTask* __restrict__ tasks, double eps,
+                                                        int chi_max, int32_t* idx_out, int idx_stride,
+                                                        double* lam_out, double* sraw_out, int lam_stride,
+                                                        TruncOut* out) {
+  const JacobiTask t = tasks[blockIdx.x];
+  truncate_body(t.X, t.m, t.n, eps, chi_max, idx_out + (size_t)blockIdx.x * idx_stride,
+                lam_out + (size_t)blockIdx.x * lam_stride, sraw_out + (size_t)blockIdx.x * lam_stride,
+                out + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) truncate_tasks_kernel(const TruncTask* __restrict__ tasks) {
+  const TruncTask t = tasks[blockIdx.x];
+  truncate_body(t.X, t.m, t.n, t.eps, t.chi_max, t.idx, t.lam, t.sraw, t.out);
 }
 
 __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __restrict__ descs) {
@@ -854,6 +897,19 @@ cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, i
   }
   truncate_kernel<<<ntasks, 1024, smem, stream>>>(d_tasks, eps, chi_max, d_idx, idx_stride, d_lam, d_sraw,
                                                   lam_stride, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_truncate_tasks(const TruncTask* d_tasks, int ntasks, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = TR_MAX * (sizeof(double) + sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(truncate_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  truncate_tasks_kernel<<<ntasks, 1024, smem, stream>>>(d_tasks);
   return cudaGetLastError();
 }
 

@@ -19,10 +19,13 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <queue>
 #include <string>
+#include <thread>
 #include <vector>
 
 using cplx = std::complex<double>;
@@ -128,6 +131,155 @@ struct pc_ctx {
   std::string last_error;
 };
 
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Workspaces.  Every factorisation of a wave (Sec. II.B.1) needs scratch of the size of its
+// own bond matrix; it is bump-allocated from a device arena per launch, so one workspace
+// serves updates of any mix of bond dimensions, from one circuit or from many.
+struct TaskScratch {
+  double2* X = nullptr;      // the Jacobi matrix: the rows of the bond matrix, or its columns
+  double2* T0 = nullptr;     // merged and gated, without lambda
+  double2* Q = nullptr;      // accumulated rotations (column path, FP32 preconditioning)
+  double2* Qb = nullptr;     // Newton-Schulz second buffer
+  double2* Y = nullptr;      // Q X after preconditioning
+  float2* X32 = nullptr;
+  float2* Q32 = nullptr;
+  double* nrm2 = nullptr;
+  double* lam = nullptr;
+  double* sraw = nullptr;
+  int32_t* idx = nullptr;
+};
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Arena bytes of one update whose bond matrix is m x n.
+size_t task_bytes(int m, int n, bool precond) {
+  const size_t v = (size_t)std::min(m, n), mn = (size_t)m * n;
+  size_t b = 2 * al256(mn * sizeof(double2)) + al256(v * v * sizeof(double2)) + 3 * al256(v * sizeof(double)) +
+             al256(v * sizeof(int32_t));
+  if (precond)
+    b += al256(mn * sizeof(float2)) + al256(v * v * sizeof(float2)) + al256(v * v * sizeof(double2)) +
+         al256(mn * sizeof(double2));
+  return b;
+}
+
+struct Workspace {
+  int cap = 0;                     // tasks per launch
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* d_arena = nullptr;
+  size_t arena_alloc = 0;          // bytes allocated
+  size_t arena_limit = 0;          // bytes a launch may use (the arena grows up to this)
+  void* d_tcws = nullptr;          // split operands of the tensor-core merge
+  size_t tcws_bytes = 0;
+  cplx* h_ops = nullptr;
+  double2* d_ops = nullptr;
+  pc::UpdateTask *h_tasks = nullptr, *d_tasks = nullptr;
+  pc::GemmDesc *h_merge = nullptr, *d_merge = nullptr;
+  pc::JacobiTask *h_jt = nullptr, *d_jt = nullptr;       // merged matrices
+  pc::JacobiTask *h_jsub = nullptr, *d_jsub = nullptr;   // preconditioned subset
+  pc::JacobiTask *h_jy = nullptr, *d_jy = nullptr;       // FP64 sweeps
+  pc::JacobiTask *h_jfb = nullptr, *d_jfb = nullptr;     // FP64-only redo subset
+  pc::JacobiTask32 *h_j32 = nullptr, *d_j32 = nullptr;
+  double2 **h_q64 = nullptr, **d_q64 = nullptr;
+  pc::GemmDesc *h_ns = nullptr, *d_ns = nullptr;         // [5][cap]
+  pc::TruncTask *h_tt = nullptr, *d_tt = nullptr;        // [2][cap]: main, redo
+  pc::TruncOut *h_tout = nullptr, *d_tout = nullptr;
+  pc::JacobiStatus *h_jst = nullptr, *d_jst = nullptr;   // [2][cap]
+  double *h_fro2 = nullptr, *d_fro2 = nullptr;
+  pc::SplitRowsDesc *h_split = nullptr, *d_split = nullptr;
+  pc::GemmDesc *h_gemm2 = nullptr, *d_gemm2 = nullptr;
+  unsigned int* d_bar = nullptr;
+  int *d_err = nullptr, *h_err = nullptr;                // [0] Jacobi barrier, [1] tensor-core merge
+  // kernel accounting: 0 merge+gate, 1 factorisation, 2 truncation, 3 split, 4 other
+  bool timing = false;
+  cudaEvent_t ev[6] = {};
+  int64_t t_launch[5] = {};
+  double t_ms[5] = {};
+  double t_flops[5] = {};
+  int64_t n_launches = 0;          // combined launches (batch accounting)
+  int64_t n_tasks = 0;
+  int max_tasks_seen = 0;
+};
+
+void ws_destroy(Workspace* w) {
+  if (!w) return;
+  cudaFree(w->d_arena); cudaFree(w->d_tcws); cudaFree(w->d_ops); cudaFree(w->d_tasks); cudaFree(w->d_merge);
+  cudaFree(w->d_jt); cudaFree(w->d_jsub); cudaFree(w->d_jy); cudaFree(w->d_jfb); cudaFree(w->d_j32);
+  cudaFree(w->d_q64); cudaFree(w->d_ns); cudaFree(w->d_tt); cudaFree(w->d_tout); cudaFree(w->d_jst);
+  cudaFree(w->d_fro2); cudaFree(w->d_split); cudaFree(w->d_gemm2); cudaFree(w->d_bar); cudaFree(w->d_err);
+  cudaFreeHost(w->h_ops); cudaFreeHost(w->h_tasks); cudaFreeHost(w->h_merge); cudaFreeHost(w->h_jt);
+  cudaFreeHost(w->h_jsub); cudaFreeHost(w->h_jy); cudaFreeHost(w->h_jfb); cudaFreeHost(w->h_j32);
+  cudaFreeHost(w->h_q64); cudaFreeHost(w->h_ns); cudaFreeHost(w->h_tt); cudaFreeHost(w->h_tout);
+  cudaFreeHost(w->h_jst); cudaFreeHost(w->h_fro2); cudaFreeHost(w->h_split); cudaFreeHost(w->h_gemm2);
+  cudaFreeHost(w->h_err);
+  for (auto& e : w->ev) if (e) cudaEventDestroy(e);
+  if (w->own_stream && w->stream) cudaStreamDestroy(w->stream);
+  delete w;
+}
+
+// A workspace for `cap` tasks per launch whose arena may grow to `arena_limit` bytes.
+// stream: the stream to launch on (nullptr: the workspace creates its own).
+cudaError_t ws_create(int cap, size_t arena_limit, int sm_count, cudaStream_t stream, Workspace** out) {
+  *out = nullptr;
+  auto* w = new Workspace();
+  w->cap = cap;
+  w->arena_limit = arena_limit;
+  w->sm_count = sm_count;
+  cudaError_t e = cudaSuccess;
+  auto dev = [&](auto** p, size_t n) { if (e == cudaSuccess) e = cudaMalloc((void**)p, n * sizeof(**p)); };
+  auto pin = [&](auto** p, size_t n) { if (e == cudaSuccess) e = cudaMallocHost((void**)p, n * sizeof(**p)); };
+  if (stream) {
+    w->stream = stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+    w->own_stream = e == cudaSuccess;
+  }
+  const size_t C = (size_t)cap;
+  dev(&w->d_ops, C * 256); pin(&w->h_ops, C * 256);
+  dev(&w->d_tasks, C); pin(&w->h_tasks, C);
+  dev(&w->d_merge, C); pin(&w->h_merge, C);
+  dev(&w->d_jt, C); pin(&w->h_jt, C);
+  dev(&w->d_jsub, C); pin(&w->h_jsub, C);
+  dev(&w->d_jy, C); pin(&w->h_jy, C);
+  dev(&w->d_jfb, C); pin(&w->h_jfb, C);
+  dev(&w->d_j32, C); pin(&w->h_j32, C);
+  dev(&w->d_q64, C); pin(&w->h_q64, C);
+  dev(&w->d_ns, 5 * C); pin(&w->h_ns, 5 * C);
+  dev(&w->d_tt, 2 * C); pin(&w->h_tt, 2 * C);
+  dev(&w->d_tout, C); pin(&w->h_tout, C);
+  dev(&w->d_jst, 2 * C); pin(&w->h_jst, 2 * C);
+  dev(&w->d_fro2, C); pin(&w->h_fro2, C);
+  dev(&w->d_split, C); pin(&w->h_split, C);
+  dev(&w->d_gemm2, C); pin(&w->h_gemm2, C);
+  dev(&w->d_bar, 2);
+  dev(&w->d_err, 2); pin(&w->h_err, 2);
+  for (auto& ev : w->ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e != cudaSuccess) { ws_destroy(w); return e; }
+  *out = w;
+  return cudaSuccess;
+}
+
+// Grows the arena to at least `bytes` (never beyond what a launch may use).
+cudaError_t ws_reserve(Workspace* w, size_t bytes) {
+  if (bytes <= w->arena_alloc) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(w->stream);
+  if (e != cudaSuccess) return e;
+  cudaFree(w->d_arena);
+  w->d_arena = nullptr;
+  w->arena_alloc = 0;
+  e = cudaMalloc(&w->d_arena, bytes);
+  if (e == cudaSuccess) w->arena_alloc = bytes;
+  return e;
+}
+
+}  // namespace
+
+struct pc_batch;
+
 struct pc_circuit {
   pc_ctx* ctx = nullptr;
   int n = 0;
@@ -143,57 +295,16 @@ struct pc_circuit {
   bool oneq_done = true;
   Layout lay[2];
   std::vector<int> chi;           // chi[k], k = 0..n: left bond of site k; chi[0] = chi[n] = 1
+  std::vector<int> cap;           // capacity of chi[k] in the site store
   std::vector<size_t> site_off;   // element offset of each site slot
   cudaStream_t stream = nullptr;
-  // device memory
   double2* d_sites = nullptr;
   double* d_lam = nullptr;        // bond b spectrum at d_lam + b * chi_max
-  double2* d_X = nullptr;
-  double2* d_T0 = nullptr;
-  double2* d_Q = nullptr;         // Jacobi accumulators (transposed path)
-  // FP32 preconditioning scratch (per task)
-  float2* d_X32 = nullptr;
-  float2* d_Q32 = nullptr;
-  double2* d_Qb = nullptr;
-  double2* d_Y = nullptr;
-  pc::JacobiTask32* d_jt32 = nullptr;
-  double2** d_q64ptr = nullptr;
-  pc::GemmDesc* d_ns = nullptr;   // 5 GEMM stages x tasks
-  pc::JacobiTask32* h_jt32 = nullptr;
-  double2** h_q64ptr = nullptr;
-  pc::GemmDesc* h_ns = nullptr;
-  // Descriptors for the FP64 sweeps after preconditioning.  A pinned staging buffer is never
-  // rewritten while an asynchronous copy from it may still be pending, so this phase has its
-  // own buffer instead of patching h_jtasks.
-  pc::JacobiTask* h_jtasks_y = nullptr;
-  double* d_xfro2 = nullptr;
-  double* h_xfro2 = nullptr;
-  double* d_nrm = nullptr;        // Jacobi squared row norms
-  size_t scratch_elems = 0;       // per task
-  double2* d_ops = nullptr;
-  pc::UpdateTask* d_tasks = nullptr;
-  pc::JacobiTask* d_jtasks = nullptr;
-  pc::GemmDesc* d_gemm = nullptr;
-  pc::GemmDesc* d_gemm2 = nullptr;
-  pc::SplitRowsDesc* d_split = nullptr;
-  pc::JacobiStatus* d_jst = nullptr;
-  pc::TruncOut* d_tout = nullptr;
-  int32_t* d_idx = nullptr;
-  double* d_lamnew = nullptr;
-  double* d_sraw = nullptr;
-  unsigned int* d_bar = nullptr;
-  int* d_err = nullptr;
   double2* d_g2 = nullptr;
-  // pinned staging
-  cplx* h_ops = nullptr;
-  pc::UpdateTask* h_tasks = nullptr;
-  pc::JacobiTask* h_jtasks = nullptr;
-  pc::GemmDesc* h_gemm = nullptr;
-  pc::GemmDesc* h_gemm2 = nullptr;
-  pc::SplitRowsDesc* h_split = nullptr;
-  pc::JacobiStatus* h_jst = nullptr;
-  pc::TruncOut* h_tout = nullptr;
-  int* h_err = nullptr;
+  pc::GemmDesc* h_gemm = nullptr; // [2] the circuit's own GEMMs (projection, sampling)
+  pc::GemmDesc* d_gemm = nullptr;
+  Workspace* ws = nullptr;        // private workspace, created by the first standalone wave
+  pc_batch* batch = nullptr;      // set while the circuit's waves go through a batch launcher
   // output MPS (environments)
   bool projected = false;
   double2* d_env = nullptr;
@@ -204,12 +315,8 @@ struct pc_circuit {
   std::vector<std::array<int32_t, 4>> unswap_log;
   pc_stats stats{};
   int stage = 0;
-  // kernel timers
   bool timing = false;
-  cudaEvent_t ev[6] = {};
-  int64_t t_launch[5] = {};
-  double t_ms[5] = {};
-  double t_flops[5] = {};
+  int64_t other_launches = 0;     // class 4 launches on the circuit's own stream
   // device-side checkpoint
   double2* d_snap_sites = nullptr;
   double* d_snap_lam = nullptr;
@@ -250,23 +357,31 @@ int max_bond(const pc_circuit* c) {
   return m;
 }
 
+// Capacity of bond k (left of site k) in the site store: 1 at the two ends, chi_max inside.
+int bond_cap(int n, int k, int chi_max) { return (k <= 0 || k >= n) ? 1 : chi_max; }
+
+// Device bytes of a circuit's store: sites at their caps, spectra, right environments
+// (allocated at projection), the peak-search pool and the buffers of n_samples samples.
+size_t store_bytes(int n, int chi_max, int64_t n_samples) {
+  size_t b = 0, env = 0;
+  for (int j = 0; j < n; ++j) {
+    const size_t cl = bond_cap(n, j, chi_max), cr = bond_cap(n, j + 1, chi_max);
+    b += cl * 4 * cr * sizeof(double2);
+    env += cl * cl * sizeof(double2);
+  }
+  b += (size_t)std::max(1, n - 1) * chi_max * sizeof(double) + env + (size_t)chi_max * chi_max * sizeof(double2);
+  b += (size_t)4096 * chi_max * sizeof(double2);
+  b += (size_t)std::min<int64_t>(n_samples, 4096) * chi_max * 5 * sizeof(double2);
+  return b;
+}
+
 void free_circuit(pc_circuit* c) {
   if (!c) return;
-  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_X); cudaFree(c->d_T0); cudaFree(c->d_Q); cudaFree(c->d_nrm);
-  cudaFree(c->d_X32); cudaFree(c->d_Q32); cudaFree(c->d_Qb); cudaFree(c->d_Y); cudaFree(c->d_jt32);
-  cudaFree(c->d_q64ptr); cudaFree(c->d_ns); cudaFree(c->d_xfro2); cudaFreeHost(c->h_xfro2);
-  cudaFreeHost(c->h_jtasks_y);
-  cudaFreeHost(c->h_jt32); cudaFreeHost(c->h_q64ptr); cudaFreeHost(c->h_ns); cudaFree(c->d_ops);
-  cudaFree(c->d_tasks); cudaFree(c->d_jtasks); cudaFree(c->d_gemm); cudaFree(c->d_gemm2);
-  cudaFree(c->d_split); cudaFree(c->d_jst); cudaFree(c->d_tout); cudaFree(c->d_idx);
-  cudaFree(c->d_lamnew); cudaFree(c->d_sraw); cudaFree(c->d_bar); cudaFree(c->d_err); cudaFree(c->d_g2);
+  ws_destroy(c->ws);
+  cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_g2); cudaFree(c->d_gemm); cudaFreeHost(c->h_gemm);
   cudaFree(c->d_env);
   cudaFree(c->d_snap_sites);
   cudaFree(c->d_snap_lam);
-  cudaFreeHost(c->h_ops); cudaFreeHost(c->h_tasks); cudaFreeHost(c->h_jtasks); cudaFreeHost(c->h_gemm);
-  cudaFreeHost(c->h_gemm2); cudaFreeHost(c->h_split); cudaFreeHost(c->h_jst); cudaFreeHost(c->h_tout);
-  cudaFreeHost(c->h_err);
-  for (auto& e : c->ev) if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -275,63 +390,35 @@ pc_status alloc_circuit(pc_circuit* c) {
   pc_ctx* ctx = c->ctx;
   const int n = c->n, X = c->chi_max;
   c->chi.assign(n + 1, 1);
+  c->cap.resize(n + 1);
+  for (int k = 0; k <= n; ++k) c->cap[k] = bond_cap(n, k, X);
   c->site_off.resize(n + 1);
   size_t off = 0;
   for (int j = 0; j < n; ++j) {
     c->site_off[j] = off;
-    const size_t cl = j == 0 ? 1 : X, cr = j == n - 1 ? 1 : X;
-    off += cl * 4 * cr;
+    off += (size_t)c->cap[j] * 4 * c->cap[j + 1];
   }
   c->site_off[n] = off;
   c->max_tasks = std::max(1, std::min(n / 2, 32));
-  c->scratch_elems = (size_t)(4 * X) * (4 * X);
-  const int T = c->max_tasks;
   CUDA_TRY(ctx, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   CUDA_TRY(ctx, cudaMalloc(&c->d_sites, off * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_lam, (size_t)std::max(1, n - 1) * X * sizeof(double)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_X, (size_t)T * c->scratch_elems * sizeof(double2)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_T0, (size_t)T * c->scratch_elems * sizeof(double2)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_Q, (size_t)T * c->scratch_elems * sizeof(double2)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_nrm, (size_t)T * 4 * X * sizeof(double)));
-  if (ctx->cfg.fp32_precondition) {
-    CUDA_TRY(ctx, cudaMalloc(&c->d_X32, (size_t)T * c->scratch_elems * sizeof(float2)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_Q32, (size_t)T * c->scratch_elems * sizeof(float2)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_Qb, (size_t)T * c->scratch_elems * sizeof(double2)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_Y, (size_t)T * c->scratch_elems * sizeof(double2)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_jt32, T * sizeof(pc::JacobiTask32)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_q64ptr, T * sizeof(double2*)));
-    CUDA_TRY(ctx, cudaMalloc(&c->d_ns, 5 * T * sizeof(pc::GemmDesc)));
-    CUDA_TRY(ctx, cudaMallocHost(&c->h_jt32, T * sizeof(pc::JacobiTask32)));
-    CUDA_TRY(ctx, cudaMallocHost(&c->h_q64ptr, T * sizeof(double2*)));
-    CUDA_TRY(ctx, cudaMallocHost(&c->h_ns, 5 * T * sizeof(pc::GemmDesc)));
-    CUDA_TRY(ctx, cudaMallocHost(&c->h_jtasks_y, T * sizeof(pc::JacobiTask)));
-  }
-  CUDA_TRY(ctx, cudaMalloc(&c->d_xfro2, T * sizeof(double)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_xfro2, T * sizeof(double)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_ops, (size_t)T * 256 * sizeof(double2)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_tasks, T * sizeof(pc::UpdateTask)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_jtasks, T * sizeof(pc::JacobiTask)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_gemm, T * sizeof(pc::GemmDesc)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_gemm2, T * sizeof(pc::GemmDesc)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_split, T * sizeof(pc::SplitRowsDesc)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_jst, T * sizeof(pc::JacobiStatus)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_tout, T * sizeof(pc::TruncOut)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_idx, (size_t)T * 4 * X * sizeof(int32_t)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_lamnew, (size_t)T * 4 * X * sizeof(double)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_sraw, (size_t)T * 4 * X * sizeof(double)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_bar, 2 * sizeof(unsigned int)));
-  CUDA_TRY(ctx, cudaMalloc(&c->d_err, sizeof(int)));
   CUDA_TRY(ctx, cudaMalloc(&c->d_g2, 4 * sizeof(double2)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_ops, (size_t)T * 256 * sizeof(cplx)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_tasks, T * sizeof(pc::UpdateTask)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_jtasks, T * sizeof(pc::JacobiTask)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_gemm, T * sizeof(pc::GemmDesc)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_gemm2, T * sizeof(pc::GemmDesc)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_split, T * sizeof(pc::SplitRowsDesc)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_jst, T * sizeof(pc::JacobiStatus)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_tout, T * sizeof(pc::TruncOut)));
-  CUDA_TRY(ctx, cudaMallocHost(&c->h_err, sizeof(int)));
-  for (auto& e : c->ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+  CUDA_TRY(ctx, cudaMalloc(&c->d_gemm, 2 * sizeof(pc::GemmDesc)));
+  CUDA_TRY(ctx, cudaMallocHost(&c->h_gemm, 2 * sizeof(pc::GemmDesc)));
+  return PC_OK;
+}
+
+// The private workspace of a circuit that runs its waves itself: max_tasks tasks per launch,
+// arena for max_tasks of its largest bond matrices.
+pc_status private_workspace(pc_circuit* c) {
+  if (c->ws) return PC_OK;
+  int big = 1;
+  for (int k = 1; k < c->n; ++k) big = std::max(big, c->cap[k]);
+  const bool precond = c->ctx->cfg.fp32_precondition && 4 * big >= 64;
+  const size_t limit = (size_t)c->max_tasks * task_bytes(4 * big, 4 * big, precond);
+  CUDA_TRY(c->ctx, ws_create(c->max_tasks, limit, c->ctx->sm_count, c->stream, &c->ws));
+  c->ws->timing = c->timing;
   return PC_OK;
 }
 
@@ -358,266 +445,522 @@ pc_status reset_identity(pc_circuit* c) {
   return PC_OK;
 }
 
-void timer_mark(pc_circuit* c, int i) {
-  if (c->timing) cudaEventRecord(c->ev[i], c->stream);
-}
+inline void count_launch(pc_circuit* c, int k = 1) { c->other_launches += k; }
 
-// Kernel launch accounting per class (0 merge+gate, 1 Jacobi, 2 truncate, 3 split, 4 other).
-inline void count_launch(pc_circuit* c, int cls, int k = 1) { c->t_launch[cls] += k; }
-
-// One wave: factorise every task (merge, gate, Jacobi, truncate), then split the ones that
-// are committed.  `accept` (may be null) decides per task from its count; counts returned.
+// One update of a wave: bond j and its 16x16 operator.
 struct WaveItem {
   int bond;
   cplx op[256];
 };
 
-pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vector<int>& counts,
-                   const std::vector<int>* commit_mask_in, bool decide_by_accept, bool accept_equal,
-                   std::vector<int>* accepted_out) {
-  pc_ctx* ctx = c->ctx;
-  const int T = (int)items.size();
-  counts.assign(T, 0);
-  if (T == 0) return PC_OK;
-  if (T > c->max_tasks) return fail(ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
-  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_len = 0, total_pairs = 0;
+// One circuit's share of a wave: factorise every item, then split the committed ones.
+// commit_mask (may be null: commit all) or, with decide_by_accept, the unswap rule decides
+// per item from its count (strict: count < chi, equal: count <= chi).
+struct WaveReq {
+  pc_circuit* c = nullptr;
+  const std::vector<WaveItem>* items = nullptr;
+  const std::vector<int>* commit_mask = nullptr;
+  bool decide_by_accept = false;
+  bool accept_equal = false;
+  std::vector<int> counts, accepted;
+  pc_status status = PC_OK;
+  bool done = false;
+};
+
+struct FlatTask {
+  WaveReq* r;
+  int k;
+};
+
+void timer_mark(Workspace* w, int i) {
+  if (w->timing) cudaEventRecord(w->ev[i], w->stream);
+}
+
+// Records an error on every circuit of a chunk.
+pc_status chunk_fail(std::vector<FlatTask>& flat, size_t b0, size_t b1, pc_status st, const std::string& msg) {
+  for (size_t i = b0; i < b1; ++i) {
+    flat[i].r->status = st;
+    fail(flat[i].r->c->ctx, st, msg);
+  }
+  return st;
+}
+
+#define WS_TRY(expr)                                                                             \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return chunk_fail(flat, b0, b1, e_ == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+// Factorises and commits the tasks flat[b0, b1) in one set of launches on w->stream.
+pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t b1) {
+  const int T = (int)(b1 - b0);
+  cudaStream_t s = w->stream;
+  std::vector<TaskScratch> sc(T);
+  std::vector<char> precond(T, 0), tc(T, 0);
+  std::vector<int> m_of(T), n_of(T), v_of(T), bond_of(T);
+  size_t need = 0;
   for (int t = 0; t < T; ++t) {
-    const int j = items[t].bond;
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const int j = (*f.r->items)[f.k].bond;
+    const int m = 4 * c->chi[j], n = 4 * c->chi[j + 2];
+    precond[t] = c->ctx->cfg.fp32_precondition && std::min(m, n) >= 64;
+    need += task_bytes(m, n, precond[t]);
+  }
+  WS_TRY(ws_reserve(w, need));
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = w->d_arena + off;
+    off += al256(bytes);
+    return p;
+  };
+  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_v = 0, max_len = 0, total_pairs = 0;
+  int tc_m = 0, tc_n = 0, tc_k = 0;
+  std::vector<pc::GemmDesc> g64, gtc;
+  for (int t = 0; t < T; ++t) {
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const WaveItem& it = (*f.r->items)[f.k];
+    const int j = it.bond;
     const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
-    std::memcpy(c->h_ops + (size_t)t * 256, items[t].op, 256 * sizeof(cplx));
-    pc::UpdateTask& u = c->h_tasks[t];
+    const int m = 4 * cl, n = 4 * cr, v = std::min(m, n), L = std::max(m, n);
+    const bool transposed = m > n;
+    m_of[t] = m; n_of[t] = n; v_of[t] = v; bond_of[t] = j;
+    tc[t] = c->ctx->cfg.precision == PC_PRECISION_TF32X3;
+    TaskScratch& x = sc[t];
+    x.X = (double2*)take((size_t)m * n * sizeof(double2));
+    x.T0 = (double2*)take((size_t)m * n * sizeof(double2));
+    x.Q = (double2*)take((size_t)v * v * sizeof(double2));
+    x.nrm2 = (double*)take((size_t)v * sizeof(double));
+    x.lam = (double*)take((size_t)v * sizeof(double));
+    x.sraw = (double*)take((size_t)v * sizeof(double));
+    x.idx = (int32_t*)take((size_t)v * sizeof(int32_t));
+    if (precond[t]) {
+      x.X32 = (float2*)take((size_t)m * n * sizeof(float2));
+      x.Q32 = (float2*)take((size_t)v * v * sizeof(float2));
+      x.Qb = (double2*)take((size_t)v * v * sizeof(double2));
+      x.Y = (double2*)take((size_t)m * n * sizeof(double2));
+    }
+    std::memcpy(w->h_ops + (size_t)t * 256, it.op, 256 * sizeof(cplx));
+    pc::UpdateTask& u = w->h_tasks[t];
     u.Bl = site_ptr(c, j);
     u.Br = site_ptr(c, j + 1);
     u.lam_l = j > 0 ? lam_ptr(c, j - 1) : nullptr;
-    u.op = reinterpret_cast<const double2*>(c->d_ops) + (size_t)t * 256;
-    u.X = c->d_X + (size_t)t * c->scratch_elems;
-    u.T0 = c->d_T0 + (size_t)t * c->scratch_elems;
+    u.op = w->d_ops + (size_t)t * 256;
+    u.X = x.X;
+    u.T0 = x.T0;
     u.chi_l = cl; u.chi_m = cm; u.chi_r = cr;
-    u.m = 4 * cl; u.n = 4 * cr;
-    u.transposed = u.m > u.n ? 1 : 0;
-    pc::GemmDesc& g = c->h_gemm[t];
-    g.A = u.Bl; g.B = u.Br; g.C = u.X; g.row_scale = nullptr;
-    g.M = 4 * cl; g.N = 4 * cr; g.K = cm;
-    g.lda = cm; g.ldb = 4 * cr; g.ldc = 4 * cr;
-    g.opB = 0; g.alpha = 1.0; g.beta = 0.0; g.D = nullptr;
+    u.m = m; u.n = n;
+    u.transposed = transposed ? 1 : 0;
+    pc::GemmDesc g{};
+    g.A = u.Bl; g.B = u.Br; g.C = u.X;
+    g.M = m; g.N = n; g.K = cm;
+    g.lda = cm; g.ldb = n; g.ldc = n;
+    g.opB = 0; g.alpha = 1.0; g.beta = 0.0;
+    if (tc[t]) {
+      gtc.push_back(g);
+      tc_m = std::max(tc_m, m); tc_n = std::max(tc_n, n); tc_k = std::max(tc_k, cm);
+    } else {
+      g64.push_back(g);
+    }
     // The Jacobi orthogonalises min(m, n) vectors: the rows of X, or for a tall bond matrix
     // its columns, with the rotations accumulated into Q (the right singular vectors).
-    pc::JacobiTask& jt = c->h_jtasks[t];
-    jt.X = u.X;
-    jt.Q = u.transposed ? c->d_Q + (size_t)t * c->scratch_elems : nullptr;
-    jt.nrm2 = c->d_nrm + (size_t)t * 4 * c->chi_max;
-    jt.fro2 = c->d_xfro2 + t;
-    jt.m = u.transposed ? u.n : u.m;
-    jt.n = u.transposed ? u.m : u.n;
-    jt.mp = jt.m + (jt.m & 1);
+    pc::JacobiTask& jt = w->h_jt[t];
+    jt.X = x.X;
+    jt.Q = transposed ? x.Q : nullptr;
+    jt.nrm2 = x.nrm2;
+    jt.fro2 = w->d_fro2 + t;
+    jt.m = v;
+    jt.n = L;
+    jt.mp = v + (v & 1);
     jt.pad_ = 0;
-    {
-      const double r = ctx->cfg.eps / (10.0 * jt.m);
-      jt.dead_rel = r * r;
-    }
-    max_m = std::max(max_m, u.m); max_n = std::max(max_n, u.n);
-    max_len = std::max(max_len, jt.n);
-    total_pairs += jt.mp / 2;
+    const double r = c->ctx->cfg.eps / (10.0 * v);
+    jt.dead_rel = r * r;
+    pc::TruncTask& tt = w->h_tt[t];
+    tt.X = precond[t] ? x.Y : x.X;
+    tt.idx = x.idx; tt.lam = x.lam; tt.sraw = x.sraw;
+    tt.out = w->d_tout + t;
+    tt.eps = c->ctx->cfg.eps;
+    tt.m = v; tt.n = L;
+    tt.chi_max = c->chi_max;
+    tt.pad_ = 0;
+    max_m = std::max(max_m, m); max_n = std::max(max_n, n); max_v = std::max(max_v, v);
+    max_len = std::max(max_len, L);
     max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
+    total_pairs += jt.mp / 2;
+    w->t_flops[0] += 8.0 * m * (double)cm * n + 8.0 * 256.0 * cl * (double)cr;
+    w->t_flops[1] += 4.0 * (4.0 * (double)L * L * v + 22.0 * (double)v * v * v);
   }
-  cudaStream_t s = c->stream;
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_ops, c->h_ops, (size_t)T * 256 * sizeof(cplx), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_tasks, c->h_tasks, T * sizeof(pc::UpdateTask), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
-  CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
-  CUDA_TRY(ctx, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-  timer_mark(c, 0);
-  CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, T, max_m, max_n, s));
-  CUDA_TRY(ctx, pc::launch_gate_apply(c->d_tasks, T, max_cl, max_cr, s));
-  count_launch(c, 0, 2);
-  int max_vec = 0;
-  for (int t = 0; t < T; ++t) max_vec = std::max(max_vec, c->h_jtasks[t].m);
+  const int n64 = (int)g64.size(), ntc = (int)gtc.size();
+  for (int i = 0; i < n64; ++i) w->h_merge[i] = g64[i];
+  for (int i = 0; i < ntc; ++i) w->h_merge[n64 + i] = gtc[i];
+  if (ntc > 0) {
+    const size_t tb = pc::tc_merge_workspace_bytes(ntc, tc_m, tc_n, tc_k);
+    if (tb > w->tcws_bytes) {
+      WS_TRY(cudaStreamSynchronize(s));
+      cudaFree(w->d_tcws);
+      w->d_tcws = nullptr;
+      w->tcws_bytes = 0;
+      WS_TRY(cudaMalloc(&w->d_tcws, tb));
+      w->tcws_bytes = tb;
+    }
+  }
+  WS_TRY(cudaMemcpyAsync(w->d_ops, w->h_ops, (size_t)T * 256 * sizeof(cplx), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_tasks, w->h_tasks, T * sizeof(pc::UpdateTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_merge, w->h_merge, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_jt, w->h_jt, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_tt, w->h_tt, T * sizeof(pc::TruncTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemsetAsync(w->d_err, 0, 2 * sizeof(int), s));
+  timer_mark(w, 0);
+  if (n64 > 0) {
+    int mm = 0, nn = 0;
+    for (auto& g : g64) { mm = std::max(mm, g.M); nn = std::max(nn, g.N); }
+    WS_TRY(pc::launch_gemm(w->d_merge, n64, mm, nn, s));
+    w->t_launch[0] += 1;
+  }
+  if (ntc > 0) {
+    // merge as complex 3xTF32 on the tensor cores (two launches: operand split, MMA)
+    WS_TRY(pc::launch_tc_merge(w->d_merge + n64, ntc, tc_m, tc_n, tc_k, w->d_tcws, w->tcws_bytes, w->d_err + 1, s));
+    w->t_launch[0] += 2;
+  }
+  WS_TRY(pc::launch_gate_apply(w->d_tasks, T, max_cl, max_cr, s));
+  w->t_launch[0] += 1;
+  timer_mark(w, 1);
+  WS_TRY(pc::launch_fro2(w->d_jt, T, w->d_fro2, s));
+  WS_TRY(pc::launch_init_accumulators(w->d_jt, T, max_v, s));
+  w->t_launch[1] += 1;
+  w->t_launch[4] += 1;
+  // FP32 preconditioning of the tasks with enough vectors: FP32 sweeps with the rotations
+  // accumulated in Q32; Q = polar(Q32) in FP64 by two Newton-Schulz steps
+  // Q <- 1.5 Q - 0.5 (Q Q^H) Q; Y = Q X; then the FP64 sweeps run on Y.
+  std::vector<int> psub;
+  for (int t = 0; t < T; ++t)
+    if (precond[t]) psub.push_back(t);
+  const int P = (int)psub.size();
+  int pv = 0, pl = 0, ppairs = 0;
+  for (int i = 0; i < P; ++i) {
+    const int t = psub[i];
+    const pc::JacobiTask& jt = w->h_jt[t];
+    const TaskScratch& x = sc[t];
+    w->h_jsub[i] = jt;
+    pc::JacobiTask32& j32 = w->h_j32[i];
+    j32.X = x.X32;
+    j32.Q = x.Q32;
+    j32.nrm2 = reinterpret_cast<float*>(x.nrm2);
+    j32.fro2 = jt.fro2;
+    j32.dead_rel = 1e-12 / jt.m;      // FP32 noise: a preconditioner may skip any pair
+    j32.m = jt.m; j32.n = jt.n; j32.mp = jt.mp; j32.pad_ = 0;
+    w->h_q64[i] = x.Q;
+    const int v = jt.m, L = jt.n;
+    double2 *QA = x.Q, *QB = x.Qb, *Y = x.Y;
+    auto gd = [&](int stage) -> pc::GemmDesc& { return w->h_ns[stage * P + i]; };
+    for (int k = 0; k < 5; ++k) gd(k) = pc::GemmDesc{};
+    gd(0).A = QA; gd(0).lda = v; gd(0).B = QA; gd(0).ldb = v; gd(0).opB = 1; gd(0).C = Y; gd(0).ldc = v;
+    gd(0).M = v; gd(0).N = v; gd(0).K = v; gd(0).alpha = 1.0;
+    gd(1).A = Y; gd(1).lda = v; gd(1).B = QA; gd(1).ldb = v; gd(1).C = QB; gd(1).ldc = v; gd(1).D = QA;
+    gd(1).M = v; gd(1).N = v; gd(1).K = v; gd(1).alpha = -0.5; gd(1).beta = 1.5;
+    gd(2).A = QB; gd(2).lda = v; gd(2).B = QB; gd(2).ldb = v; gd(2).opB = 1; gd(2).C = Y; gd(2).ldc = v;
+    gd(2).M = v; gd(2).N = v; gd(2).K = v; gd(2).alpha = 1.0;
+    gd(3).A = Y; gd(3).lda = v; gd(3).B = QB; gd(3).ldb = v; gd(3).C = QA; gd(3).ldc = v; gd(3).D = QB;
+    gd(3).M = v; gd(3).N = v; gd(3).K = v; gd(3).alpha = -0.5; gd(3).beta = 1.5;
+    gd(4).A = QA; gd(4).lda = v; gd(4).B = jt.X; gd(4).ldb = L; gd(4).C = Y; gd(4).ldc = L;
+    gd(4).M = v; gd(4).N = L; gd(4).K = v; gd(4).alpha = 1.0;
+    pv = std::max(pv, v); pl = std::max(pl, L);
+    ppairs += jt.mp / 2;
+  }
+  if (P > 0) {
+    WS_TRY(cudaMemcpyAsync(w->d_jsub, w->h_jsub, P * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemcpyAsync(w->d_j32, w->h_j32, P * sizeof(pc::JacobiTask32), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemcpyAsync(w->d_q64, w->h_q64, P * sizeof(double2*), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemcpyAsync(w->d_ns, w->h_ns, 5 * (size_t)P * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemsetAsync(w->d_jst + w->cap, 0, P * sizeof(pc::JacobiStatus), s));
+    WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+    WS_TRY(pc::launch_precond_init(w->d_jsub, w->d_j32, P, pv, pl, s));
+    WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, 40, w->d_bar, w->d_err, w->sm_count, pl, ppairs, s));
+    WS_TRY(pc::launch_widen_q(w->d_j32, w->d_q64, P, pv, s));
+    for (int k = 0; k < 4; ++k) WS_TRY(pc::launch_gemm(w->d_ns + k * P, P, pv, pv, s));
+    WS_TRY(pc::launch_gemm(w->d_ns + 4 * P, P, pv, pl, s));
+    w->t_launch[1] += 8;
+  }
+  // FP64 sweeps: on Y = Q X for the preconditioned tasks (accumulating into Q on the column
+  // path), on X itself for the others
   for (int t = 0; t < T; ++t) {
-    const pc::UpdateTask& u = c->h_tasks[t];
-    c->t_flops[0] += 8.0 * u.m * (double)u.chi_m * u.n + 8.0 * 256.0 * u.chi_l * (double)u.chi_r;
-    const double M = std::max(u.m, u.n), N = std::min(u.m, u.n);
-    c->t_flops[1] += 4.0 * (4.0 * M * M * N + 22.0 * N * N * N);
+    w->h_jy[t] = w->h_jt[t];
+    if (precond[t]) w->h_jy[t].X = sc[t].Y;
   }
-  timer_mark(c, 1);
-  // Factorise every task of the wave: optionally FP32 preconditioning, then FP64 Jacobi
-  // sweeps, then truncation.  Returns with the outputs on the host.
-  // Which matrix holds each task's factorised rows once factorise() returns.
+  WS_TRY(cudaMemcpyAsync(w->d_jy, w->h_jy, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemsetAsync(w->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
+  WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+  int max_sweeps = 1;
+  for (int t = 0; t < T; ++t) max_sweeps = std::max(max_sweeps, flat[b0 + t].r->c->ctx->cfg.jacobi_max_sweeps);
+  WS_TRY(pc::launch_jacobi(w->d_jy, T, w->d_jst, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_len, total_pairs, s));
+  w->t_launch[1] += 1;
+  timer_mark(w, 2);
+  WS_TRY(pc::launch_truncate_tasks(w->d_tt, T, s));
+  w->t_launch[2] += 1;
+  timer_mark(w, 3);
+  WS_TRY(cudaMemcpyAsync(w->h_tout, w->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_jst, w->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_err, w->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_fro2, w->d_fro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (P > 0)
+    WS_TRY(cudaMemcpyAsync(w->h_jst + w->cap, w->d_jst + w->cap, P * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < P; ++i) {
+    pc_circuit* c = flat[b0 + psub[i]].r->c;
+    c->stats.max_sweeps_fp32 = std::max(c->stats.max_sweeps_fp32, w->h_jst[w->cap + i].sweeps);
+  }
+  if (w->timing) {
+    float a = 0, b = 0, d = 0;
+    cudaEventElapsedTime(&a, w->ev[0], w->ev[1]);
+    cudaEventElapsedTime(&b, w->ev[1], w->ev[2]);
+    cudaEventElapsedTime(&d, w->ev[2], w->ev[3]);
+    w->t_ms[0] += a; w->t_ms[1] += b; w->t_ms[2] += d;
+  }
+  if (w->h_err[0]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+  if (w->h_err[1]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "a tensor-core merge wait exceeded its limit");
+  // Safety net of the preconditioning: Q X must keep the Frobenius norm of X (Q unitary).
+  // A task that fails the check is factorised again in FP64 only, from its merged matrix.
+  std::vector<int> redo;
+  for (int t = 0; t < T; ++t) {
+    if (!precond[t]) continue;
+    const double x2 = w->h_fro2[t], y2 = w->h_tout[t].total2;
+    if (!(std::fabs(y2 - x2) <= 1e-9 * x2)) redo.push_back(t);
+  }
   std::vector<double2*> final_x(T);
-  auto factorise = [&](bool precond) -> pc_status {
-    const size_t E = c->scratch_elems;
-    for (int t = 0; t < T; ++t) final_x[t] = c->h_jtasks[t].X;
-    // h_jtasks (X = the merged matrix, Q = the accumulator on the column path) is not
-    // modified after run_wave filled it
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
-    CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
-    CUDA_TRY(ctx, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    CUDA_TRY(ctx, pc::launch_fro2(c->d_jtasks, T, c->d_xfro2, s));
-    count_launch(c, 1, 1);
-    if (!precond) {
-      CUDA_TRY(ctx, pc::launch_init_accumulators(c->d_jtasks, T, max_n, s));
-      count_launch(c, 4, 1);
-    } else {
-      // FP32 sweeps with the rotations accumulated in Q32; Q = polar(Q32) in FP64 by two
-      // Newton-Schulz steps Q <- 1.5 Q - 0.5 (Q Q^H) Q; X <- Q X; then the FP64 sweeps.
-      for (int t = 0; t < T; ++t) {
-        const pc::JacobiTask& jt = c->h_jtasks[t];
-        pc::JacobiTask32& j32 = c->h_jt32[t];
-        j32.X = c->d_X32 + (size_t)t * E;
-        j32.Q = c->d_Q32 + (size_t)t * E;
-        j32.nrm2 = reinterpret_cast<float*>(jt.nrm2);
-        j32.fro2 = jt.fro2;
-        j32.dead_rel = 1e-12 / jt.m;      // FP32 noise: a preconditioner may skip any pair
-        j32.m = jt.m; j32.n = jt.n; j32.mp = jt.mp; j32.pad_ = 0;
-        double2* QA = c->d_Q + (size_t)t * E;
-        double2* QB = c->d_Qb + (size_t)t * E;
-        double2* Y = c->d_Y + (size_t)t * E;
-        c->h_q64ptr[t] = QA;
-        const int v = jt.m, L = jt.n;
-        auto gd = [&](int stage) -> pc::GemmDesc& { return c->h_ns[stage * T + t]; };
-        for (int k = 0; k < 5; ++k) gd(k) = pc::GemmDesc{};
-        gd(0).A = QA; gd(0).lda = v; gd(0).B = QA; gd(0).ldb = v; gd(0).opB = 1; gd(0).C = Y; gd(0).ldc = v;
-        gd(0).M = v; gd(0).N = v; gd(0).K = v; gd(0).alpha = 1.0;
-        gd(1).A = Y; gd(1).lda = v; gd(1).B = QA; gd(1).ldb = v; gd(1).C = QB; gd(1).ldc = v; gd(1).D = QA;
-        gd(1).M = v; gd(1).N = v; gd(1).K = v; gd(1).alpha = -0.5; gd(1).beta = 1.5;
-        gd(2).A = QB; gd(2).lda = v; gd(2).B = QB; gd(2).ldb = v; gd(2).opB = 1; gd(2).C = Y; gd(2).ldc = v;
-        gd(2).M = v; gd(2).N = v; gd(2).K = v; gd(2).alpha = 1.0;
-        gd(3).A = Y; gd(3).lda = v; gd(3).B = QB; gd(3).ldb = v; gd(3).C = QA; gd(3).ldc = v; gd(3).D = QB;
-        gd(3).M = v; gd(3).N = v; gd(3).K = v; gd(3).alpha = -0.5; gd(3).beta = 1.5;
-        gd(4).A = QA; gd(4).lda = v; gd(4).B = jt.X; gd(4).ldb = L; gd(4).C = Y; gd(4).ldc = L;
-        gd(4).M = v; gd(4).N = L; gd(4).K = v; gd(4).alpha = 1.0;
-      }
-      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jt32, c->h_jt32, T * sizeof(pc::JacobiTask32), cudaMemcpyHostToDevice, s));
-      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_q64ptr, c->h_q64ptr, T * sizeof(double2*), cudaMemcpyHostToDevice, s));
-      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_ns, c->h_ns, 5 * T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
-      CUDA_TRY(ctx, pc::launch_precond_init(c->d_jtasks, c->d_jt32, T, max_vec, max_len, s));
-      CUDA_TRY(ctx, pc::launch_jacobi32(c->d_jt32, T, c->d_jst, 40, c->d_bar, c->d_err, ctx->sm_count, max_len,
-                                        total_pairs, s));
-      CUDA_TRY(ctx, pc::launch_widen_q(c->d_jt32, c->d_q64ptr, T, max_vec, s));
-      for (int k = 0; k < 4; ++k) CUDA_TRY(ctx, pc::launch_gemm(c->d_ns + k * T, T, max_vec, max_vec, s));
-      CUDA_TRY(ctx, pc::launch_gemm(c->d_ns + 4 * T, T, max_vec, max_len, s));
-      count_launch(c, 1, 8);
-      // the FP64 sweeps run on Y = Q X, accumulating into Q on the column path
-      for (int t = 0; t < T; ++t) {
-        c->h_jtasks_y[t] = c->h_jtasks[t];
-        c->h_jtasks_y[t].X = c->d_Y + (size_t)t * E;
-        final_x[t] = c->h_jtasks_y[t].X;
-      }
-      CUDA_TRY(ctx, cudaMemcpyAsync(c->d_jtasks, c->h_jtasks_y, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
-      CUDA_TRY(ctx, cudaMemsetAsync(c->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
-      CUDA_TRY(ctx, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s));
+  for (int t = 0; t < T; ++t) final_x[t] = precond[t] ? sc[t].Y : sc[t].X;
+  if (!redo.empty()) {
+    const int R = (int)redo.size();
+    int rv = 0, rl = 0, rpairs = 0;
+    for (int i = 0; i < R; ++i) {
+      const int t = redo[i];
+      w->h_jfb[i] = w->h_jt[t];
+      w->h_tt[w->cap + i] = w->h_tt[t];
+      w->h_tt[w->cap + i].X = sc[t].X;
+      final_x[t] = sc[t].X;
+      rv = std::max(rv, w->h_jt[t].m); rl = std::max(rl, w->h_jt[t].n);
+      rpairs += w->h_jt[t].mp / 2;
+      flat[b0 + t].r->c->stats.fallbacks += 1;
     }
-    CUDA_TRY(ctx, pc::launch_jacobi(c->d_jtasks, T, c->d_jst, ctx->cfg.jacobi_max_sweeps, c->d_bar, c->d_err,
-                                    ctx->sm_count, max_len, total_pairs, s));
-    count_launch(c, 1, 1);
-    timer_mark(c, 2);
-    const int stride = 4 * c->chi_max;
-    CUDA_TRY(ctx, pc::launch_truncate(c->d_jtasks, T, ctx->cfg.eps, c->chi_max, c->d_idx, stride, c->d_lamnew,
-                                      c->d_sraw, stride, c->d_tout, s));
-    count_launch(c, 2, 1);
-    timer_mark(c, 3);
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_tout, c->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_jst, c->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->h_xfro2, c->d_xfro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if (c->timing) {
-      float a = 0, b = 0, d = 0;
-      cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
-      cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
-      cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
-      c->t_ms[0] += a; c->t_ms[1] += b; c->t_ms[2] += d;
-    }
-    if (*c->h_err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
-    return PC_OK;
-  };
-  const bool want_precond = ctx->cfg.fp32_precondition && max_vec >= 64;
-  pc_status fst = factorise(want_precond);
-  if (fst != PC_OK) return fst;
-  if (want_precond) {
-    // Safety net: Q X must keep the Frobenius norm of X (Q unitary).  Otherwise redo the
-    // wave in FP64 only.
-    bool ok = true;
-    for (int t = 0; t < T; ++t) {
-      const double x2 = c->h_xfro2[t], y2 = c->h_tout[t].total2;
-      if (!(std::fabs(y2 - x2) <= 1e-9 * x2)) ok = false;
-    }
-    if (!ok) {
-      c->stats.fallbacks += 1;
-      timer_mark(c, 1);
-      fst = factorise(false);
-      if (fst != PC_OK) return fst;
-    }
+    WS_TRY(cudaMemcpyAsync(w->d_jfb, w->h_jfb, R * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemcpyAsync(w->d_tt + w->cap, w->h_tt + w->cap, R * sizeof(pc::TruncTask), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemsetAsync(w->d_jst + w->cap, 0, R * sizeof(pc::JacobiStatus), s));
+    WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+    WS_TRY(pc::launch_init_accumulators(w->d_jfb, R, rv, s));
+    WS_TRY(pc::launch_jacobi(w->d_jfb, R, w->d_jst + w->cap, max_sweeps, w->d_bar, w->d_err, w->sm_count, rl, rpairs, s));
+    WS_TRY(pc::launch_truncate_tasks(w->d_tt + w->cap, R, s));
+    w->t_launch[1] += 1; w->t_launch[2] += 1; w->t_launch[4] += 1;
+    WS_TRY(cudaMemcpyAsync(w->h_tout, w->d_tout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
+    WS_TRY(cudaMemcpyAsync(w->h_jst + w->cap, w->d_jst + w->cap, R * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+    WS_TRY(cudaMemcpyAsync(w->h_err, w->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    WS_TRY(cudaStreamSynchronize(s));
+    if (w->h_err[0]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+    for (int i = 0; i < R; ++i) w->h_jst[redo[i]] = w->h_jst[w->cap + i];
   }
-  const int stride = 4 * c->chi_max;
+  // counts, convergence and commit decisions
+  std::vector<char> commit(T, 0);
   for (int t = 0; t < T; ++t) {
-    counts[t] = c->h_tout[t].count;
-    c->stats.max_sweeps = std::max(c->stats.max_sweeps, c->h_jst[t].sweeps);
-    if (!c->h_jst[t].converged)
-      return fail(ctx, PC_ERR_NOCONVERGE, "one-sided Jacobi reached the sweep cap on bond " + std::to_string(items[t].bond));
-  }
-  // commit decisions
-  std::vector<int> commit(T, 1);
-  if (commit_mask_in) commit = *commit_mask_in;
-  if (decide_by_accept) {
-    for (int t = 0; t < T; ++t) {
-      const int old = c->chi[items[t].bond + 1];
-      commit[t] = accept_equal ? (counts[t] <= old) : (counts[t] < old);
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const int cnt = w->h_tout[t].count;
+    f.r->counts[f.k] = cnt;
+    c->stats.max_sweeps = std::max(c->stats.max_sweeps, w->h_jst[t].sweeps);
+    if (!w->h_jst[t].converged) {
+      const pc::JacobiStatus& js = w->h_jst[t];
+      f.r->status = fail(c->ctx, PC_ERR_NOCONVERGE,
+                         "one-sided Jacobi reached the sweep cap on bond " + std::to_string(bond_of[t]) + " (" +
+                             std::to_string(m_of[t]) + " x " + std::to_string(n_of[t]) + ", " +
+                             std::to_string(js.sweeps) + " sweeps, rotations in the last three: " +
+                             std::to_string(js.rot[0]) + " " + std::to_string(js.rot[1]) + " " +
+                             std::to_string(js.rot[2]) + ")");
+      continue;
     }
+    bool ok = f.r->commit_mask ? (*f.r->commit_mask)[f.k] != 0 : true;
+    if (f.r->decide_by_accept) {
+      const int old = c->chi[bond_of[t] + 1];
+      ok = f.r->accept_equal ? (cnt <= old) : (cnt < old);
+    }
+    f.r->accepted[f.k] = ok ? 1 : 0;
+    commit[t] = ok && f.r->status == PC_OK;
   }
-  if (accepted_out) *accepted_out = commit;
   int nc = 0, max_cnt = 0, max_nn = 0, max_mm = 0;
   for (int t = 0; t < T; ++t) {
     if (!commit[t]) continue;
-    const int j = items[t].bond;
-    const pc::UpdateTask& u = c->h_tasks[t];
-    const int cnt = counts[t];
-    pc::SplitRowsDesc& sd = c->h_split[nc];
+    pc_circuit* c = flat[b0 + t].r->c;
+    const int j = bond_of[t];
+    const int cnt = w->h_tout[t].count;
+    const int m = m_of[t], n = n_of[t];
+    pc::SplitRowsDesc& sd = w->h_split[nc];
     sd.X = final_x[t];
-    sd.Q = u.transposed ? c->h_jtasks[t].Q : nullptr;
+    sd.Q = m > n ? sc[t].Q : nullptr;
     sd.dst = site_ptr(c, j + 1);
-    sd.idx = c->d_idx + (size_t)t * stride;
-    sd.sraw = c->d_sraw + (size_t)t * stride;
+    sd.idx = sc[t].idx;
+    sd.sraw = sc[t].sraw;
     sd.count = cnt;
-    sd.n = u.n;
-    pc::GemmDesc& g = c->h_gemm2[nc];
-    g.A = u.T0; g.B = sd.dst; g.C = site_ptr(c, j); g.row_scale = nullptr;
-    g.M = u.m; g.N = cnt; g.K = u.n;
-    g.lda = u.n; g.ldb = u.n; g.ldc = cnt;
-    g.opB = 1; g.alpha = 1.0 / c->h_tout[t].nrm; g.beta = 0.0; g.D = nullptr;
-    max_cnt = std::max(max_cnt, cnt); max_nn = std::max(max_nn, u.n); max_mm = std::max(max_mm, u.m);
-    c->t_flops[3] += 8.0 * u.m * (double)u.n * cnt;
+    sd.n = n;
+    pc::GemmDesc& g = w->h_gemm2[nc];
+    g = pc::GemmDesc{};
+    g.A = sc[t].T0; g.B = sd.dst; g.C = site_ptr(c, j); g.row_scale = nullptr;
+    g.M = m; g.N = cnt; g.K = n;
+    g.lda = n; g.ldb = n; g.ldc = cnt;
+    g.opB = 1; g.alpha = 1.0 / w->h_tout[t].nrm; g.beta = 0.0; g.D = nullptr;
+    max_cnt = std::max(max_cnt, cnt); max_nn = std::max(max_nn, n); max_mm = std::max(max_mm, m);
+    w->t_flops[3] += 8.0 * m * (double)n * cnt;
     ++nc;
   }
   if (nc > 0) {
-    timer_mark(c, 4);
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_split, c->h_split, nc * sizeof(pc::SplitRowsDesc), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm2, c->h_gemm2, nc * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(ctx, pc::launch_split_rows(c->d_split, nc, max_cnt, max_nn, s));
-    CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm2, nc, max_mm, max_cnt, s));
-    count_launch(c, 3, 2);
+    timer_mark(w, 4);
+    WS_TRY(cudaMemcpyAsync(w->d_split, w->h_split, nc * sizeof(pc::SplitRowsDesc), cudaMemcpyHostToDevice, s));
+    WS_TRY(cudaMemcpyAsync(w->d_gemm2, w->h_gemm2, nc * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+    WS_TRY(pc::launch_split_rows(w->d_split, nc, max_cnt, max_nn, s));
+    WS_TRY(pc::launch_gemm(w->d_gemm2, nc, max_mm, max_cnt, s));
+    w->t_launch[3] += 2;
     for (int t = 0; t < T; ++t) {
       if (!commit[t]) continue;
-      const int j = items[t].bond;
-      CUDA_TRY(ctx, cudaMemcpyAsync(lam_ptr(c, j), c->d_lamnew + (size_t)t * stride, counts[t] * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, s));
-      c->chi[j + 1] = counts[t];
+      pc_circuit* c = flat[b0 + t].r->c;
+      const int j = bond_of[t];
+      WS_TRY(cudaMemcpyAsync(lam_ptr(c, j), sc[t].lam, w->h_tout[t].count * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      c->chi[j + 1] = w->h_tout[t].count;
     }
-    timer_mark(c, 5);
-    if (c->timing) {
-      // the split is measured at the next synchronisation point
-      CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    timer_mark(w, 5);
+    if (w->timing) {
+      WS_TRY(cudaStreamSynchronize(s));
       float e = 0;
-      cudaEventElapsedTime(&e, c->ev[4], c->ev[5]);
-      c->t_ms[3] += e;
+      cudaEventElapsedTime(&e, w->ev[4], w->ev[5]);
+      w->t_ms[3] += e;
     }
   }
-  c->stats.max_chi = std::max(c->stats.max_chi, max_bond(c));
-  c->stats.n_waves += 1;
-  c->projected = false;
+  // circuits with their own stream read these sites next: finish before returning to them
+  bool foreign = false;
+  for (int t = 0; t < T; ++t) foreign |= flat[b0 + t].r->c->stream != s;
+  if (foreign) WS_TRY(cudaStreamSynchronize(s));
+  w->n_launches += 1;
+  w->n_tasks += T;
+  w->max_tasks_seen = std::max(w->max_tasks_seen, T);
   return PC_OK;
+}
+
+// Runs the waves of several circuits together (their items are pairwise disjoint within
+// each circuit; circuits share nothing), in chunks that fit the workspace.
+pc_status execute_waves(Workspace* w, std::vector<WaveReq*>& reqs) {
+  std::vector<FlatTask> flat;
+  for (WaveReq* r : reqs) {
+    r->status = PC_OK;
+    r->counts.assign(r->items->size(), 0);
+    r->accepted.assign(r->items->size(), 0);
+    for (int k = 0; k < (int)r->items->size(); ++k) flat.push_back({r, k});
+  }
+  size_t pos = 0;
+  pc_status worst = PC_OK;
+  while (pos < flat.size()) {
+    size_t end = pos, need = 0;
+    while (end < flat.size() && (int)(end - pos) < w->cap) {
+      const FlatTask& f = flat[end];
+      pc_circuit* c = f.r->c;
+      const int j = (*f.r->items)[f.k].bond;
+      const int m = 4 * c->chi[j], n = 4 * c->chi[j + 2];
+      const size_t b = task_bytes(m, n, c->ctx->cfg.fp32_precondition && std::min(m, n) >= 64);
+      if (need + b > w->arena_limit && end > pos) break;
+      need += b;
+      ++end;
+    }
+    pc_status st = run_chunk(w, flat, pos, end);
+    if (st != PC_OK) worst = st;
+    pos = end;
+  }
+  for (WaveReq* r : reqs) {
+    r->c->stats.n_waves += 1;
+    r->c->stats.max_chi = std::max(r->c->stats.max_chi, max_bond(r->c));
+    r->c->projected = false;
+  }
+  return worst;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Batch launcher: circuits attached to a batch post their waves here; one host thread
+// combines the waves posted by every participating circuit into one set of launches.
+struct pc_batch {
+  pc_ctx* ctx = nullptr;
+  Workspace* ws = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_post, cv_done;
+  std::vector<WaveReq*> pending;
+  int participants = 0;           // circuits inside a contraction that will post waves
+  bool stop = false;
+  double window_s = 0.002;        // longest wait for the remaining participants' waves
+  std::thread launcher;
+};
+
+namespace {
+
+void batch_loop(pc_batch* b) {
+  cudaSetDevice(b->ctx->cfg.device);
+  std::unique_lock<std::mutex> lk(b->mu);
+  for (;;) {
+    b->cv_post.wait(lk, [&] { return b->stop || !b->pending.empty(); });
+    if (b->pending.empty()) break;   // stop requested and nothing left
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(b->window_s);
+    b->cv_post.wait_until(lk, deadline, [&] { return b->stop || (int)b->pending.size() >= b->participants; });
+    std::vector<WaveReq*> reqs;
+    reqs.swap(b->pending);
+    lk.unlock();
+    execute_waves(b->ws, reqs);
+    lk.lock();
+    for (WaveReq* r : reqs) r->done = true;
+    b->cv_done.notify_all();
+  }
+}
+
+void batch_enter(pc_batch* b) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->participants += 1;
+}
+
+void batch_leave(pc_batch* b) {
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->participants -= 1;
+  }
+  b->cv_post.notify_all();
+}
+
+// One circuit's wave: through its batch launcher if attached, else on its own workspace.
+pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vector<int>& counts,
+                   const std::vector<int>* commit_mask, bool decide_by_accept, bool accept_equal,
+                   std::vector<int>* accepted_out) {
+  counts.assign(items.size(), 0);
+  if (items.empty()) return PC_OK;
+  if ((int)items.size() > c->max_tasks) return fail(c->ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
+  WaveReq req;
+  req.c = c;
+  req.items = &items;
+  req.commit_mask = commit_mask;
+  req.decide_by_accept = decide_by_accept;
+  req.accept_equal = accept_equal;
+  pc_status st;
+  if (c->batch) {
+    pc_batch* b = c->batch;
+    // the circuit's own stream may still hold copies into its sites (restore, set-up)
+    CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+    std::unique_lock<std::mutex> lk(b->mu);
+    b->pending.push_back(&req);
+    b->cv_post.notify_all();
+    b->cv_done.wait(lk, [&] { return req.done; });
+    st = req.status;
+  } else {
+    st = private_workspace(c);
+    if (st != PC_OK) return st;
+    std::vector<WaveReq*> one{&req};
+    execute_waves(c->ws, one);
+    st = req.status;
+  }
+  counts = req.counts;
+  if (accepted_out) *accepted_out = req.accepted;
+  return st;
 }
 
 }  // namespace
@@ -702,7 +1045,7 @@ pc_status apply_oneq_layer(pc_circuit* c) {
     const int j = c->lay[PC_SIDE_LEFT].pos[c->oneq_q[k]];
     CUDA_TRY(c->ctx, cudaMemcpyAsync(c->d_g2, &c->oneq_m[4 * k], 4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c->ctx, pc::launch_one_site(site_ptr(c, j), c->chi[j], c->chi[j + 1], c->d_g2, PC_SIDE_LEFT, c->stream));
-    count_launch(c, 4);
+    count_launch(c);
     CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
   }
   c->projected = false;
@@ -875,7 +1218,7 @@ pc_status project(pc_circuit* c) {
       CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cr, c->stream));
       CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
-      count_launch(c, 4, 2);
+      count_launch(c, 2);
       c->h_gemm[0] = g2;
       CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, cl, cl, c->stream));
@@ -912,13 +1255,15 @@ void pc_default_config(pc_config* cfg) {
   cfg->jacobi_max_sweeps = 60;
   cfg->device = 0;
   cfg->fp32_precondition = 1;
+  cfg->precision = PC_PRECISION_FP64;
 }
 
 pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
   if (!cfg || !out) return PC_ERR_INVALID_ARG;
   *out = nullptr;
   if (!(cfg->eps >= 0.0) || cfg->chi_max < 1 || cfg->chi_max > 1024 || !(cfg->tau > 0.0) ||
-      cfg->max_unswap_iter < 0 || cfg->jacobi_max_sweeps < 1 || cfg->unswap_mode < 0 || cfg->unswap_mode > 2)
+      cfg->max_unswap_iter < 0 || cfg->jacobi_max_sweeps < 1 || cfg->unswap_mode < 0 || cfg->unswap_mode > 2 ||
+      cfg->precision < PC_PRECISION_FP64 || cfg->precision > PC_PRECISION_TF32X3)
     return PC_ERR_INVALID_ARG;
   auto* ctx = new pc_ctx();
   ctx->cfg = *cfg;
@@ -1010,6 +1355,13 @@ pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
   const double t0 = now_s();
   c->stats = pc_stats{};
+  // while it contracts, an attached circuit is one of the batch's participants: the launcher
+  // waits (briefly) for its waves to combine them with the others'
+  struct Participation {
+    pc_batch* b;
+    explicit Participation(pc_batch* bb) : b(bb) { if (b) batch_enter(b); }
+    ~Participation() { if (b) batch_leave(b); }
+  } participation(c->batch);
   const double tau = ctx->cfg.tau;
   pc_status st = PC_OK;
   for (int32_t it = 0; it < max_iterations && layers_remain(c); ++it) {
@@ -1267,7 +1619,7 @@ pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, 
   CUDA_TRY(ctx, cudaMalloc(&pool, (size_t)cap_slots * CH * sizeof(double2)));
   CUDA_TRY(ctx, cudaMalloc(&d_marg, 2 * sizeof(double)));
   CUDA_TRY(ctx, pc::launch_fill_ones(pool, 1, c->stream));
-  count_launch(c, 4);
+  count_launch(c);
   int64_t used = 1;
   heap.push(Node{1.0, {}, 0});
   int64_t expansions = 0;
@@ -1300,7 +1652,7 @@ pc_status pc_extract_peak(pc_circuit* c, int64_t max_expansions, uint8_t* bits, 
     double2* w1 = pool + (size_t)(used + 1) * CH;
     cudaError_t e = pc::launch_expand(pool + (size_t)top.slot * CH, site_ptr(c, j), cl, cr, c->d_env + c->env_off[j + 1],
                                       w0, w1, d_marg, c->stream);
-    count_launch(c, 4);
+    count_launch(c);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hm, d_marg, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { cudaFree(pool); cudaFree(d_marg); return fail(ctx, PC_ERR_CUDA, cudaGetErrorString(e)); }
@@ -1335,7 +1687,7 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
     return fail(ctx, PC_ERR_OOM, "sampling buffers");
   }
   cudaError_t e = pc::launch_fill_ones(V, rows, c->stream);
-  count_launch(c, 4);
+  count_launch(c);
   for (int j = 0; j < n && e == cudaSuccess; ++j) {
     const int cl = c->chi[j], cr = c->chi[j + 1];
     pc::GemmDesc g[2];
@@ -1350,7 +1702,7 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
     c->h_gemm[1] = g[1];
     e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, 2 * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 2, rows, cr, c->stream);
-    count_launch(c, 4);
+    count_launch(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) break;
     if (sampling) {
@@ -1364,14 +1716,14 @@ pc_status sweep_rows(pc_circuit* c, int rows, const double* d_u, uint8_t* d_site
         e = cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = pc::launch_gemm(c->d_gemm, 1, rows, cr, c->stream);
         if (e == cudaSuccess) e = pc::launch_quadform_rows(q.A, Y, rows, cr, cr, sg ? m1 : m0, c->stream);
-        count_launch(c, 4, 2);
+        count_launch(c, 2);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       }
       if (e == cudaSuccess) e = pc::launch_sample_pick(W0, W1, m0, m1, d_u, rows, cr, j, n, V2, d_site_bits, c->stream);
     } else {
       e = pc::launch_amp_pick(W0, W1, d_site_bits, rows, cr, j, n, V2, c->stream);
     }
-    count_launch(c, 4);
+    count_launch(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     std::swap(V, V2);
   }
@@ -1453,12 +1805,114 @@ pc_status pc_amplitudes(pc_circuit* c, int64_t k, const uint8_t* bits, double* a
   return PC_OK;
 }
 
+pc_status pc_batch_create(pc_ctx* ctx, int32_t max_tasks, int64_t arena_bytes, pc_batch** out) {
+  if (!ctx || !out || max_tasks < 1 || max_tasks > 256 || arena_bytes < 0) return PC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
+  auto* b = new pc_batch();
+  b->ctx = ctx;
+  const size_t limit = arena_bytes > 0 ? (size_t)arena_bytes : (size_t)8 << 30;
+  cudaError_t e = ws_create(max_tasks, limit, ctx->sm_count, nullptr, &b->ws);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(ctx, e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  b->launcher = std::thread(batch_loop, b);
+  *out = b;
+  return PC_OK;
+}
+
+pc_status pc_batch_destroy(pc_batch* b) {
+  if (!b) return PC_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->stop = true;
+  }
+  b->cv_post.notify_all();
+  if (b->launcher.joinable()) b->launcher.join();
+  ws_destroy(b->ws);
+  delete b;
+  return PC_OK;
+}
+
+pc_status pc_batch_attach(pc_batch* b, pc_circuit* c) {
+  if (!b || check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
+  if (c->batch && c->batch != b) return fail(c->ctx, PC_ERR_STATE, "circuit is attached to another batch");
+  if (c->ctx->cfg.device != b->ctx->cfg.device) return fail(c->ctx, PC_ERR_INVALID_ARG, "batch on another device");
+  c->batch = b;
+  return PC_OK;
+}
+
+pc_status pc_batch_detach(pc_batch* b, pc_circuit* c) {
+  if (!b || check_circuit(c) != PC_OK || c->batch != b) return PC_ERR_INVALID_ARG;
+  c->batch = nullptr;
+  return PC_OK;
+}
+
+pc_status pc_batch_contract(pc_batch* b, int32_t n, pc_circuit* const* circuits, pc_status* statuses,
+                            pc_stats* stats) {
+  if (!b || n < 0 || (n > 0 && (!circuits || !statuses))) return PC_ERR_INVALID_ARG;
+  for (int32_t k = 0; k < n; ++k) {
+    if (check_circuit(circuits[k]) != PC_OK) return PC_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < k; ++i)
+      if (circuits[i] == circuits[k]) return PC_ERR_INVALID_ARG;
+  }
+  for (int32_t k = 0; k < n; ++k) {
+    pc_status st = pc_batch_attach(b, circuits[k]);
+    if (st != PC_OK) {
+      for (int32_t i = 0; i < k; ++i) pc_batch_detach(b, circuits[i]);
+      return st;
+    }
+  }
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int32_t k = 0; k < n; ++k)
+    th.emplace_back([=] {
+      pc_stats local{};
+      statuses[k] = pc_contract(circuits[k], &local);
+      if (stats) stats[k] = local;
+    });
+  for (auto& t : th) t.join();
+  for (int32_t k = 0; k < n; ++k) pc_batch_detach(b, circuits[k]);
+  pc_status worst = PC_OK;
+  for (int32_t k = 0; k < n; ++k)
+    if (statuses[k] < 0) worst = statuses[k];
+  return worst;
+}
+
+pc_status pc_batch_counters(pc_batch* b, int64_t* launches, int64_t* tasks, int32_t* max_tasks, double* ms,
+                            double* flops) {
+  if (!b) return PC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (launches) *launches = b->ws->n_launches;
+  if (tasks) *tasks = b->ws->n_tasks;
+  if (max_tasks) *max_tasks = b->ws->max_tasks_seen;
+  for (int k = 0; k < 5; ++k) {
+    if (ms) ms[k] = b->ws->t_ms[k];
+    if (flops) flops[k] = b->ws->t_flops[k];
+  }
+  return PC_OK;
+}
+
+pc_status pc_batch_set_timing(pc_batch* b, int32_t enable) {
+  if (!b) return PC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->ws->timing = enable != 0;
+  return PC_OK;
+}
+
+int64_t pc_projected_bytes(int32_t n_qubits, int32_t chi_max, int64_t n_samples) {
+  if (n_qubits < 2 || chi_max < 1 || n_samples < 0) return -1;
+  return (int64_t)store_bytes(n_qubits, chi_max, n_samples);
+}
+
 pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops) {
   if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
   for (int k = 0; k < 5; ++k) {
-    if (launches) launches[k] = c->t_launch[k];
-    if (ms) ms[k] = c->t_ms[k];
-    if (flops) flops[k] = c->t_flops[k];
+    const Workspace* w = c->ws;
+    if (launches) launches[k] = (w ? w->t_launch[k] : 0) + (k == 4 ? c->other_launches : 0);
+    if (ms) ms[k] = w ? w->t_ms[k] : 0.0;
+    if (flops) flops[k] = w ? w->t_flops[k] : 0.0;
   }
   return PC_OK;
 }
@@ -1471,8 +1925,12 @@ pc_status pc_get_stream(pc_circuit* c, void** stream) {
 
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable) {
   if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
-  for (int k = 0; k < 5; ++k) { c->t_launch[k] = 0; c->t_ms[k] = 0.0; c->t_flops[k] = 0.0; }
+  c->other_launches = 0;
   c->timing = enable != 0;
+  if (c->ws) {
+    for (int k = 0; k < 5; ++k) { c->ws->t_launch[k] = 0; c->ws->t_ms[k] = 0.0; c->ws->t_flops[k] = 0.0; }
+    c->ws->timing = c->timing;
+  }
   return PC_OK;
 }
 

@@ -47,10 +47,12 @@ struct UpdateTask {
 // tall bond matrix), because more vectors than dimensions cannot all be made orthogonal.
 // When Q is given (m x m, set to the identity), every rotation is also applied to the rows
 // of Q, which then holds the accumulated unitary.
-// Pairs of rows that are both below the noise floor dead2 = dead_rel * |X|_F^2 are not
-// rotated (nullptr fro2: no floor).  Any pair with a row above the floor is, so the kept
-// rows end orthogonal to everything; rows below the floor stay below the cutoff whatever
-// they combine to when dead_rel <= (eps_cut / (10 m))^2.
+// Noise floors (nullptr fro2: none): with dead2 = dead_rel * |X|_F^2 and marg2 = 6 m dead2,
+// a pair is not rotated when both rows are below dead2, or one is below dead2 and the other
+// below marg2.  With dead_rel <= (eps_cut / (10 m))^2 and eps_cut * s_0 >= eps_cut |X|_F /
+// sqrt(m): every row above marg2 ends orthogonal to every other row (its norm is a singular
+// value), the rows between the floors are mutually orthogonal, and the block of all rows
+// below marg2 has no singular value above 0.35 eps_cut s_0, so the kept set is exact.
 struct JacobiTask {
   double2* X;             // m x n row-major; rows are orthogonalised in place
   double2* Q;             // optional m x m accumulator (nullptr: none)
@@ -116,6 +118,20 @@ cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max,
                             int32_t* d_idx, int idx_stride, double* d_lam, double* d_sraw,
                             int lam_stride, TruncOut* d_out, cudaStream_t stream);
+// Truncation of a batch whose tasks carry their own cutoff, cap and output buffers (tasks
+// of several circuits in one launch).
+struct TruncTask {
+  const double2* X;       // orthogonalised rows, m x n row-major
+  int32_t* idx;           // kept row indices in descending order of norm [count]
+  double* lam;            // kept values normalised to unit 2-norm [count]
+  double* sraw;           // kept values, unnormalised [count]
+  TruncOut* out;
+  double eps;
+  int32_t m, n;
+  int32_t chi_max;
+  int32_t pad_;
+};
+cudaError_t launch_truncate_tasks(const TruncTask* d_tasks, int ntasks, cudaStream_t stream);
 // B_{j+1}'[k][c] = X[idx[k]][c] / s_idx[k] (rows path) or conj(Q[idx[k]][c]) (transposed
 // path: the accumulated right singular vectors) for each task; dst pointers per task.
 struct SplitRowsDesc {
@@ -145,5 +161,14 @@ cudaError_t launch_sample_pick(const double2* W0, const double2* W1, const doubl
 cudaError_t launch_amp_pick(const double2* W0, const double2* W1, const uint8_t* site_bits, int K,
                             int chi, int site, int n_sites, double2* Vnext, cudaStream_t stream);
 cudaError_t launch_fill_ones(double2* v, int rows, cudaStream_t stream);
+
+// Mixed-precision merge on tcgen05 tensor cores (merge_tc.cu): for each descriptor of the
+// batch, C = A * B (opB = 0, alpha = 1, beta = 0, no row scaling) as complex 3xTF32 with FP32
+// accumulation; A, B and C are FP64 in global memory.  The workspace holds the split
+// operands, tc_merge_workspace_bytes() of them for the batch's largest M, N, K.
+// err (device int) is set to 1 if a bounded wait inside the kernel gave up.
+size_t tc_merge_workspace_bytes(int T, int max_m, int max_n, int max_k);
+cudaError_t launch_tc_merge(const GemmDesc* d_desc, int T, int max_m, int max_n, int max_k, void* workspace,
+                            size_t workspace_bytes, int* d_err, cudaStream_t stream);
 
 }  // namespace pc

@@ -303,3 +303,27 @@ def peaked_saturated_state(n: int, chi_max: int, seed: int = 0, delta: float = 0
         s = np.concatenate([[1.0], np.sqrt(delta) * np.exp(-np.arange(1, k) / 64.0)])
         lam.append(s / np.linalg.norm(s))
     return B, lam
+
+
+# --- Several circuits at once (batching) and request streams (serving) ---------------------
+
+def circuit_mix(count: int, seed: int = 0, n_range=(8, 12), gates_range=(12, 24),
+                pert_range=(0.0, 0.04)) -> list[Circuit]:
+    """`count` independent hidden-permutation mirrors, each with its own qubit count, gate
+    count per half and perturbation drawn uniformly from the given ranges (inclusive for
+    the integers), its own hidden permutation and planted bitstring."""
+    rng = rng_for(13, seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        g = int(rng.integers(gates_range[0], gates_range[1] + 1))
+        e = float(rng.uniform(pert_range[0], pert_range[1]))
+        out.append(hidden_permutation_mirror(n, g, e, seed=100000 + 1000 * seed + k))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson stream of `count` requests at `rate` per
+    second: cumulative sums of exponential gaps."""
+    rng = rng_for(14, seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
