@@ -341,6 +341,11 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
       if (i == 0) { a = tk.mp - 1; b = r; }
       else { a = (r + i) % Rr; b = (r - i + Rr) % Rr; }
       const bool full = (r == 0);
+      // unchanged since this pair's check one sweep ago (then below tolerance): skip
+      if (s > 0 && a < tk.m && b < tk.m) {
+        const int prev = (int)(g - Rr);
+        if (tk.stamp[a] < prev && tk.stamp[b] < prev) continue;
+      }
       R (*red)[4] = s_red[parity][grp];
       if (a >= tk.m || b >= tk.m) {
         // the padding row: in round 0 the real row still gets its exact norm
@@ -495,6 +500,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         if (nb < JacTraits<R>::cancel * bb) nb = -nb;
         tk.nrm2[a] = na;
         tk.nrm2[b] = nb;
+        tk.stamp[a] = (int)g;
+        tk.stamp[b] = (int)g;
         atomicAdd(&st[t].rot[s % 3], 1u);
       }
     }
@@ -681,6 +688,13 @@ __global__ void init_accumulators_kernel(const JacobiTask* __restrict__ tasks) {
   t.Q[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
 }
 
+// stamp[k] = -1 for every row of every task (before a Jacobi launch).
+template <typename Task>
+__global__ void init_stamps_kernel(const Task* __restrict__ tasks) {
+  const Task t = tasks[blockIdx.y];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < t.m; e += gridDim.x * blockDim.x) t.stamp[e] = -1;
+}
+
 __global__ void one_site_kernel(double2* B, int chi_l, int chi_r, const double2* g, int side) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)chi_l * 2 * chi_r) return;
@@ -803,6 +817,18 @@ cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi
   const long long cells = (long long)max_chi_l * max_chi_r;
   dim3 grid((unsigned)((cells + 255) / 256), ntasks);
   gate_apply_kernel<<<grid, 256, 0, stream>>>(d_tasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_stamps(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  init_stamps_kernel<JacobiTask><<<dim3((max_m + 255) / 256, ntasks), 256, 0, stream>>>(d_tasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_stamps32(const JacobiTask32* d_tasks, int ntasks, int max_m, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  init_stamps_kernel<JacobiTask32><<<dim3((max_m + 255) / 256, ntasks), 256, 0, stream>>>(d_tasks);
   return cudaGetLastError();
 }
 

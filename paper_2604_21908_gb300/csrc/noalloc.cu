@@ -33,6 +33,7 @@ struct NoAllocScratch {
   int32_t idx[NA_MAX_DIM];
   double lam[NA_MAX_DIM];
   double sraw[NA_MAX_DIM];
+  int32_t stamp[NA_MAX_DIM];
   pc::JacobiTask jtask;
   pc::JacobiStatus jst;
   pc::TruncOut tout;
@@ -46,7 +47,8 @@ NoAllocScratch* g_scratch_dev[NA_MAX_DEVICES] = {};
 int g_sm_count[NA_MAX_DEVICES] = {};
 std::mutex g_setup_mutex;
 
-// Writes the task descriptor and clears everything that must start at zero.
+// Writes the task descriptor and resets everything that must start cleared (status,
+// barrier, error flag, row stamps at -1).
 __global__ void noalloc_setup_kernel(NoAllocScratch* s, int m, int n, int transposed) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   pc::JacobiTask t;
@@ -54,6 +56,8 @@ __global__ void noalloc_setup_kernel(NoAllocScratch* s, int m, int n, int transp
   t.Q = transposed ? s->Q : nullptr;
   t.nrm2 = s->nrm2;
   t.fro2 = nullptr;
+  t.stamp = s->stamp;
+  for (int k = 0; k < NA_MAX_DIM; ++k) s->stamp[k] = -1;
   t.dead_rel = 0.0;
   t.m = transposed ? n : m;
   t.n = transposed ? m : n;

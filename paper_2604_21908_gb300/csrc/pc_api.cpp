@@ -145,6 +145,8 @@ struct TaskScratch {
   double2* Y = nullptr;      // Q X after preconditioning
   float2* X32 = nullptr;
   float2* Q32 = nullptr;
+  int32_t* stamp = nullptr;      // FP64 sweeps
+  int32_t* stamp32 = nullptr;    // FP32 sweeps
   double* nrm2 = nullptr;
   double* lam = nullptr;
   double* sraw = nullptr;
@@ -157,10 +159,10 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t task_bytes(int m, int n, bool precond) {
   const size_t v = (size_t)std::min(m, n), mn = (size_t)m * n;
   size_t b = 2 * al256(mn * sizeof(double2)) + al256(v * v * sizeof(double2)) + 3 * al256(v * sizeof(double)) +
-             al256(v * sizeof(int32_t));
+             2 * al256(v * sizeof(int32_t));
   if (precond)
     b += al256(mn * sizeof(float2)) + al256(v * v * sizeof(float2)) + al256(v * v * sizeof(double2)) +
-         al256(mn * sizeof(double2));
+         al256(mn * sizeof(double2)) + al256(v * sizeof(int32_t));
   return b;
 }
 
@@ -537,7 +539,9 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     x.lam = (double*)take((size_t)v * sizeof(double));
     x.sraw = (double*)take((size_t)v * sizeof(double));
     x.idx = (int32_t*)take((size_t)v * sizeof(int32_t));
+    x.stamp = (int32_t*)take((size_t)v * sizeof(int32_t));
     if (precond[t]) {
+      x.stamp32 = (int32_t*)take((size_t)v * sizeof(int32_t));
       x.X32 = (float2*)take((size_t)m * n * sizeof(float2));
       x.Q32 = (float2*)take((size_t)v * v * sizeof(float2));
       x.Qb = (double2*)take((size_t)v * v * sizeof(double2));
@@ -572,6 +576,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     jt.Q = transposed ? x.Q : nullptr;
     jt.nrm2 = x.nrm2;
     jt.fro2 = w->d_fro2 + t;
+    jt.stamp = x.stamp;
     jt.m = v;
     jt.n = L;
     jt.mp = v + (v & 1);
@@ -650,6 +655,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     j32.Q = x.Q32;
     j32.nrm2 = reinterpret_cast<float*>(x.nrm2);
     j32.fro2 = jt.fro2;
+    j32.stamp = x.stamp32;
     j32.dead_rel = 1e-12 / jt.m;      // FP32 noise: a preconditioner may skip any pair
     j32.m = jt.m; j32.n = jt.n; j32.mp = jt.mp; j32.pad_ = 0;
     w->h_q64[i] = x.Q;
@@ -678,6 +684,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     WS_TRY(cudaMemsetAsync(w->d_jst + w->cap, 0, P * sizeof(pc::JacobiStatus), s));
     WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
     WS_TRY(pc::launch_precond_init(w->d_jsub, w->d_j32, P, pv, pl, s));
+    WS_TRY(pc::launch_init_stamps32(w->d_j32, P, pv, s));
     WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, 40, w->d_bar, w->d_err, w->sm_count, pl, ppairs, s));
     WS_TRY(pc::launch_widen_q(w->d_j32, w->d_q64, P, pv, s));
     for (int k = 0; k < 4; ++k) WS_TRY(pc::launch_gemm(w->d_ns + k * P, P, pv, pv, s));
@@ -695,6 +702,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
   WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
   int max_sweeps = 1;
   for (int t = 0; t < T; ++t) max_sweeps = std::max(max_sweeps, flat[b0 + t].r->c->ctx->cfg.jacobi_max_sweeps);
+  WS_TRY(pc::launch_init_stamps(w->d_jy, T, max_v, s));
   WS_TRY(pc::launch_jacobi(w->d_jy, T, w->d_jst, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_len, total_pairs, s));
   w->t_launch[1] += 1;
   timer_mark(w, 2);
@@ -749,6 +757,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     WS_TRY(cudaMemsetAsync(w->d_jst + w->cap, 0, R * sizeof(pc::JacobiStatus), s));
     WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
     WS_TRY(pc::launch_init_accumulators(w->d_jfb, R, rv, s));
+    WS_TRY(pc::launch_init_stamps(w->d_jfb, R, rv, s));
     WS_TRY(pc::launch_jacobi(w->d_jfb, R, w->d_jst + w->cap, max_sweeps, w->d_bar, w->d_err, w->sm_count, rl, rpairs, s));
     WS_TRY(pc::launch_truncate_tasks(w->d_tt + w->cap, R, s));
     w->t_launch[1] += 1; w->t_launch[2] += 1; w->t_launch[4] += 1;

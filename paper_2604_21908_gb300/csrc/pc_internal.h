@@ -53,11 +53,15 @@ struct UpdateTask {
 // sqrt(m): every row above marg2 ends orthogonal to every other row (its norm is a singular
 // value), the rows between the floors are mutually orthogonal, and the block of all rows
 // below marg2 has no singular value above 0.35 eps_cut s_0, so the kept set is exact.
+// stamp (m entries, set to -1 by the caller before the launch) records the round in which
+// each row was last rotated: a pair neither of whose rows changed since the pair's own
+// check one sweep earlier has the same inner product and is skipped.
 struct JacobiTask {
   double2* X;             // m x n row-major; rows are orthogonalised in place
   double2* Q;             // optional m x m accumulator (nullptr: none)
   double* nrm2;           // m squared row norms (scratch owned by the kernel)
   const double* fro2;     // squared Frobenius norm of X (or nullptr)
+  int32_t* stamp;         // m rounds of last rotation (scratch, -1 at launch)
   double dead_rel;
   int32_t m, n;
   int32_t mp;             // m rounded up to even
@@ -69,6 +73,7 @@ struct JacobiTask32 {
   float2* Q;
   float* nrm2;
   const double* fro2;
+  int32_t* stamp;
   double dead_rel;
   int32_t m, n;
   int32_t mp;
@@ -107,6 +112,9 @@ cudaError_t launch_widen_q(const JacobiTask32* d_t32, double2* const* d_q64, int
 cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
                             unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
                             cudaStream_t stream);
+// stamp[k] = -1 for every row of every task (required before each Jacobi launch).
+cudaError_t launch_init_stamps(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
+cudaError_t launch_init_stamps32(const JacobiTask32* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 // Sets every task's accumulator Q (if any) to the identity.
 cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 // Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the
