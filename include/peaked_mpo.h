@@ -57,6 +57,10 @@ typedef int32_t pc_status;
 #define PC_PRECISION_TF32X3  1    /* merges as complex 3xTF32 on tcgen05 tensor cores with */
                                   /* FP32 accumulation; factorisation and truncation FP64  */
 
+#define PC_SIDE_ALTERNATE    0    /* Algorithm 1: each step absorbs a layer of C_L, then of C_R */
+#define PC_SIDE_ADAPTIVE     1    /* App. A.3: each step tentatively absorbs the next layer of  */
+                                  /* either side and keeps the smaller size(M) (ties: left)    */
+
 #define PC_SIDE_LEFT  0           /* out-legs: M <- g M   */
 #define PC_SIDE_RIGHT 1           /* in-legs:  M <- M h   */
 #define PC_SIDE_BOTH  2
@@ -79,6 +83,9 @@ typedef struct pc_config {
                              /* (two Newton-Schulz steps) and applied, then FP64 sweeps    */
                              /* finish.  The result keeps FP64 accuracy.  0: FP64 only.     */
   int32_t precision;         /* PC_PRECISION_*: arithmetic of the two-site merge          */
+  int32_t precondition_sweeps; /* cap on FP32 preconditioning sweeps (>= 1); the FP64 sweeps */
+                             /* that follow run to convergence whatever this cap           */
+  int32_t side_mode;         /* PC_SIDE_ALTERNATE or PC_SIDE_ADAPTIVE                      */
 } pc_config;
 
 /* Counters filled by pc_contract. */
@@ -131,6 +138,25 @@ pc_status pc_contract(pc_circuit* c, pc_stats* stats);
  * remain as well as when done; *done (may be NULL) is set to 1 once every layer is absorbed.
  * stats (may be NULL) receives the counters of this call only. */
 pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats* stats, int32_t* done);
+
+/* Telemetry of the contraction (the quantities of the paper's Fig. 3: MPO size against the
+ * unitaries absorbed and against time, by phase): one record after each absorption phase and
+ * one after each unswap stage, since the circuit was loaded. */
+typedef struct pc_trace_record {
+  int32_t stage;             /* outer iteration of Algorithm 1                              */
+  int32_t phase;             /* 0 after absorption, 1 after unswapping                      */
+  int64_t gates;             /* two-qubit gates of C absorbed so far (both sides)           */
+  int64_t size;              /* size(M), total tensor elements                             */
+  int32_t max_chi;
+  int32_t accepted;          /* swaps accepted in this stage (0 after absorption)          */
+  double seconds;            /* host wall time since pc_load_gates                         */
+} pc_trace_record;
+/* rec[cap] receives up to cap records; *n_rec the full count. */
+pc_status pc_get_trace(pc_circuit* c, int64_t cap, pc_trace_record* rec, int64_t* n_rec);
+
+/* The counters of the circuit's work since its last pc_contract / pc_contract_iterations
+ * call began (updates run through pc_apply_updates included). */
+pc_status pc_get_stats(pc_circuit* c, pc_stats* stats);
 
 /* Layer cursors of the two fronts (number of layers of C_L / C_R already absorbed). */
 pc_status pc_get_cursors(pc_circuit* c, int64_t* left, int64_t* right);

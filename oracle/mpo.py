@@ -47,6 +47,7 @@ class Config:
     accept_equal: bool = False      # App. A.2 non-strict acceptance
     unswap_parallel: bool = True    # App. A.1 parallel swap selection
     unswap_enabled: bool = True     # False = the plain Middle-MPO attack (Sec. I)
+    side_adaptive: bool = False     # App. A.3 adaptive side selection (else alternate L, R)
 
 
 def two_site_operator(g: np.ndarray | None = None, h: np.ndarray | None = None) -> np.ndarray:
@@ -204,6 +205,7 @@ class Result:
     stalled: bool = False
     n_updates: int = 0
     n_trials: int = 0
+    sides: list[int] = field(default_factory=list)     # App. A.3: side absorbed per step
 
 
 class Contraction:
@@ -266,6 +268,53 @@ class Contraction:
             for gidx in self.right_layers[self.right_cursor]:
                 self._route_and_apply(SIDE_RIGHT, gidx)
             self.right_cursor += 1
+
+    def _save(self):
+        st = self.state
+        return ([b.copy() for b in st.B], [l.copy() for l in st.lam],
+                {k: (list(v.pos), list(v.site)) for k, v in self.lay.items()},
+                self.left_cursor, self.right_cursor, self.oneq_done, len(self.res.plan), self.res.n_updates)
+
+    def _load(self, saved) -> None:
+        B, lam, lays, lc, rc, oq, nplan, nup = saved
+        self.state.B = [b.copy() for b in B]
+        self.state.lam = [l.copy() for l in lam]
+        for k, (pos, site) in lays.items():
+            self.lay[k].pos[:] = pos
+            self.lay[k].site[:] = site
+        self.left_cursor, self.right_cursor, self.oneq_done = lc, rc, oq
+        del self.res.plan[nplan:]
+        self.res.n_updates = nup
+
+    def _absorb_step_adaptive(self) -> int:
+        """App. A.3: absorb the next layer of C_L and, separately, of C_R into copies of M and
+        keep the one with the smaller size(M).  Reading: ties go to the left (Algorithm 1
+        absorbs the left side first); when one side has no layer left the other is absorbed;
+        the one-qubit layer X^s counts as the last layer of C_L.  Only the kept absorption
+        appears in the plan.  Returns the side absorbed."""
+        can_l = self.left_cursor < len(self.left_layers) or not self.oneq_done
+        can_r = self.right_cursor < len(self.right_layers)
+        if not can_r:
+            self._absorb_left_layer()
+            return SIDE_LEFT
+        if not can_l:
+            self._absorb_right_layer()
+            return SIDE_RIGHT
+        base = self._save()
+        self._absorb_left_layer()
+        size_l = self.state.size()
+        after_l = self._save()
+        self._load(base)
+        self._absorb_right_layer()
+        if size_l <= self.state.size():
+            self._load(after_l)
+            return SIDE_LEFT
+        return SIDE_RIGHT
+
+    def gates_absorbed(self) -> int:
+        """Two-qubit gates of C absorbed so far (both sides; the telemetry of Fig. 3)."""
+        return (sum(len(l) for l in self.left_layers[:self.left_cursor])
+                + sum(len(l) for l in self.right_layers[:self.right_cursor]))
 
     def layers_remain(self) -> bool:
         return (self.left_cursor < len(self.left_layers) or not self.oneq_done
@@ -344,22 +393,28 @@ class Contraction:
         while self.layers_remain():
             first = True
             while (first or st.size() < cfg.tau) and self.layers_remain():
-                self._absorb_left_layer()
-                self._absorb_right_layer()
+                if cfg.side_adaptive:
+                    self.res.sides.append(self._absorb_step_adaptive())
+                else:
+                    self._absorb_left_layer()
+                    self._absorb_right_layer()
                 first = False
             self.res.trace.append({"phase": "absorb", "stage": self.stage, "size": st.size(),
                                    "max_chi": max(st.bond_dims()) if self.n > 1 else 1,
-                                   "updates": self.res.n_updates})
+                                   "updates": self.res.n_updates, "gates": self.gates_absorbed(),
+                                   "accepted": 0})
+            accepted = 0
             if cfg.unswap_enabled and self.n > 1:
                 if cfg.unswap_parallel:
-                    self.unswap_parallel()
+                    accepted = self.unswap_parallel()
                 else:
-                    self.unswap_sequential()
+                    accepted = self.unswap_sequential()
             if st.size() >= cfg.tau and self.layers_remain():
                 self.res.stalled = True
             self.res.trace.append({"phase": "unswap", "stage": self.stage, "size": st.size(),
                                    "max_chi": max(st.bond_dims()) if self.n > 1 else 1,
-                                   "updates": self.res.n_updates})
+                                   "updates": self.res.n_updates, "gates": self.gates_absorbed(),
+                                   "accepted": accepted})
             self.stage += 1
             # Rewiring (Sec. II.B.3): the remaining gates are routed with the current
             # layouts, which already hold P_L and P_R; nothing else changes.

@@ -20,13 +20,14 @@ STATUS_NAMES = {0: "PC_OK", -1: "PC_ERR_INVALID_ARG", -2: "PC_ERR_NONUNITARY", -
                 -8: "PC_ERR_STATE", 1: "PC_WARN_STALLED"}
 UNSWAP_PARALLEL, UNSWAP_SEQUENTIAL, UNSWAP_OFF = 0, 1, 2
 PRECISION_FP64, PRECISION_TF32X3 = 0, 1
+SIDE_ALTERNATE, SIDE_ADAPTIVE = 0, 1
 
 
 class PcConfig(C.Structure):
     _fields_ = [("eps", C.c_double), ("chi_max", C.c_int32), ("tau", C.c_double),
                 ("max_unswap_iter", C.c_int32), ("accept_equal", C.c_int32), ("unswap_mode", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32), ("fp32_precondition", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("precondition_sweeps", C.c_int32), ("side_mode", C.c_int32)]
 
 
 class PcStats(C.Structure):
@@ -37,6 +38,11 @@ class PcStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
+
+
+class PcTraceRecord(C.Structure):
+    _fields_ = [("stage", C.c_int32), ("phase", C.c_int32), ("gates", C.c_int64), ("size", C.c_int64),
+                ("max_chi", C.c_int32), ("accepted", C.c_int32), ("seconds", C.c_double)]
 
 
 class PcServerConfig(C.Structure):
@@ -85,7 +91,7 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_get_bond_dims", "pc_get_layouts", "pc_get_spectrum", "pc_get_site", "pc_set_state",
            "pc_apply_updates", "pc_plan_routing", "pc_get_plan", "pc_get_unswap_log", "pc_kernel_timers",
            "pc_reset_kernel_timers", "pc_contract_iterations", "pc_get_cursors", "pc_set_cursors", "pc_snapshot",
-           "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_batch_create", "pc_batch_destroy",
+           "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_get_stats", "pc_get_trace", "pc_batch_create", "pc_batch_destroy",
            "pc_batch_attach", "pc_batch_detach", "pc_batch_contract", "pc_batch_counters", "pc_batch_set_timing",
            "pc_projected_bytes", "pc_server_create", "pc_server_submit", "pc_server_wait", "pc_server_get_stats",
            "pc_server_clock", "pc_server_destroy"]
@@ -131,6 +137,8 @@ def load(path: str = LIB_PATH):
         "pc_kernel_timers": ([vp, vp, vp, vp], i32),
         "pc_contract_iterations": ([vp, i32, _p(PcStats), _p(i32)], i32),
         "pc_get_cursors": ([vp, _p(i64), _p(i64)], i32),
+        "pc_get_stats": ([vp, _p(PcStats)], i32),
+        "pc_get_trace": ([vp, i64, vp, _p(i64)], i32),
         "pc_set_cursors": ([vp, i64, i64], i32),
         "pc_snapshot": ([vp], i32),
         "pc_restore": ([vp], i32),
@@ -280,6 +288,20 @@ class Circuit:
         d = stats.as_dict()
         d["done"] = bool(done.value)
         return d
+
+    def stats(self) -> dict:
+        """pc_get_stats: counters since the last contraction call began."""
+        out = PcStats()
+        self._chk(self.lib.pc_get_stats(self.h, C.byref(out)), "pc_get_stats")
+        return out.as_dict()
+
+    def trace(self) -> list[dict]:
+        """pc_get_trace: (stage, phase, gates, size, max_chi, accepted, seconds) records."""
+        n = C.c_int64(0)
+        self._chk(self.lib.pc_get_trace(self.h, 0, None, C.byref(n)), "pc_get_trace")
+        recs = (PcTraceRecord * max(n.value, 1))()
+        self._chk(self.lib.pc_get_trace(self.h, n.value, C.cast(recs, C.c_void_p), C.byref(n)), "pc_get_trace")
+        return [{f: getattr(recs[k], f) for f, _ in PcTraceRecord._fields_} for k in range(n.value)]
 
     def cursors(self):
         a, b = C.c_int64(0), C.c_int64(0)

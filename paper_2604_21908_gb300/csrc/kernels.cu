@@ -250,6 +250,7 @@ __device__ __forceinline__ void group_sum4(R& a, R& b, R& c, R& d, R (*red)[4], 
   if constexpr (G > 1) {
     const int w = gl >> 5;
     if ((gl & 31) == 0) { red[w][0] = a; red[w][1] = b; red[w][2] = c; red[w][3] = d; }
+    __syncwarp();   // bar.sync wants each warp converged
     asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
     a = b = c = d = R(0);
 #pragma unroll
@@ -453,6 +454,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         }
       }
       if constexpr (G > 1) {
+        __syncwarp();
         asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
         if (gl >= 32) {
           const R* sh = s_rot[grp];

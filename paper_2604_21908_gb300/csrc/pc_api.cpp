@@ -317,6 +317,8 @@ struct pc_circuit {
   std::vector<std::array<int32_t, 4>> unswap_log;
   pc_stats stats{};
   int stage = 0;
+  std::vector<pc_trace_record> trace;
+  double t_loaded = 0.0;
   bool timing = false;
   int64_t other_launches = 0;     // class 4 launches on the circuit's own stream
   // device-side checkpoint
@@ -327,6 +329,17 @@ struct pc_circuit {
   Layout snap_lay[2];
   size_t snap_lcur = 0, snap_rcur = 0;
   bool snap_oneq_done = true;
+  // App. A.3 adaptive side selection: the state before a step and after its left trial
+  struct Saved {
+    double2* sites = nullptr;
+    double* lam = nullptr;
+    std::vector<int> chi;
+    Layout lay[2];
+    size_t lcur = 0, rcur = 0;
+    bool oneq_done = true;
+    size_t nplan = 0;
+    int64_t nupd = 0;
+  } saved[2];
 };
 
 namespace {
@@ -384,6 +397,7 @@ void free_circuit(pc_circuit* c) {
   cudaFree(c->d_env);
   cudaFree(c->d_snap_sites);
   cudaFree(c->d_snap_lam);
+  for (auto& sv : c->saved) { cudaFree(sv.sites); cudaFree(sv.lam); }
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -685,7 +699,10 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
     WS_TRY(pc::launch_precond_init(w->d_jsub, w->d_j32, P, pv, pl, s));
     WS_TRY(pc::launch_init_stamps32(w->d_j32, P, pv, s));
-    WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, 40, w->d_bar, w->d_err, w->sm_count, pl, ppairs, s));
+    int pre_sweeps = 1;
+    for (int i = 0; i < P; ++i)
+      pre_sweeps = std::max(pre_sweeps, flat[b0 + psub[i]].r->c->ctx->cfg.precondition_sweeps);
+    WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count, pl, ppairs, s));
     WS_TRY(pc::launch_widen_q(w->d_j32, w->d_q64, P, pv, s));
     for (int k = 0; k < 4; ++k) WS_TRY(pc::launch_gemm(w->d_ns + k * P, P, pv, pv, s));
     WS_TRY(pc::launch_gemm(w->d_ns + 4 * P, P, pv, pl, s));
@@ -1061,8 +1078,103 @@ pc_status apply_oneq_layer(pc_circuit* c) {
   return PC_OK;
 }
 
+int64_t gates_absorbed(const pc_circuit* c) {
+  int64_t g = 0;
+  for (size_t k = 0; k < c->lcur; ++k) g += (int64_t)c->left_layers[k].size();
+  for (size_t k = 0; k < c->rcur; ++k) g += (int64_t)c->right_layers[k].size();
+  return g;
+}
+
+void trace_point(pc_circuit* c, int phase, int accepted) {
+  c->trace.push_back({c->stage, phase, gates_absorbed(c), mpo_size(c), max_bond(c), accepted, now_s() - c->t_loaded});
+}
+
 bool layers_remain(const pc_circuit* c) {
   return c->lcur < c->left_layers.size() || !c->oneq_done || c->rcur < c->right_layers.size();
+}
+
+pc_status absorb_left_layer(pc_circuit* c) {
+  if (c->lcur < c->left_layers.size()) {
+    auto ops = plan_layer(PC_SIDE_LEFT, c->left_layers[c->lcur], c->pairs.data(), c->lay[PC_SIDE_LEFT]);
+    c->lcur++;
+    return apply_resolved(c, ops);
+  }
+  if (!c->oneq_done) {
+    pc_status st = apply_oneq_layer(c);
+    if (st != PC_OK) return st;
+    c->oneq_done = true;
+  }
+  return PC_OK;
+}
+
+pc_status absorb_right_layer(pc_circuit* c) {
+  if (c->rcur < c->right_layers.size()) {
+    auto ops = plan_layer(PC_SIDE_RIGHT, c->right_layers[c->rcur], c->pairs.data(), c->lay[PC_SIDE_RIGHT]);
+    c->rcur++;
+    return apply_resolved(c, ops);
+  }
+  return PC_OK;
+}
+
+// Device copy of the contraction state into / out of saved slot k (the circuit's stream).
+pc_status save_state(pc_circuit* c, int k) {
+  pc_circuit::Saved& sv = c->saved[k];
+  const size_t nsite = c->site_off[c->n], nlam = (size_t)std::max(1, c->n - 1) * c->chi_max;
+  if (!sv.sites) {
+    CUDA_TRY(c->ctx, cudaMalloc(&sv.sites, nsite * sizeof(double2)));
+    CUDA_TRY(c->ctx, cudaMalloc(&sv.lam, nlam * sizeof(double)));
+  }
+  CUDA_TRY(c->ctx, cudaMemcpyAsync(sv.sites, c->d_sites, nsite * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c->ctx, cudaMemcpyAsync(sv.lam, c->d_lam, nlam * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  sv.chi = c->chi;
+  sv.lay[0] = c->lay[0];
+  sv.lay[1] = c->lay[1];
+  sv.lcur = c->lcur;
+  sv.rcur = c->rcur;
+  sv.oneq_done = c->oneq_done;
+  sv.nplan = c->plan_log.size();
+  sv.nupd = c->stats.n_updates;
+  return PC_OK;
+}
+
+pc_status load_state(pc_circuit* c, int k) {
+  pc_circuit::Saved& sv = c->saved[k];
+  const size_t nsite = c->site_off[c->n], nlam = (size_t)std::max(1, c->n - 1) * c->chi_max;
+  CUDA_TRY(c->ctx, cudaMemcpyAsync(c->d_sites, sv.sites, nsite * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c->ctx, cudaMemcpyAsync(c->d_lam, sv.lam, nlam * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->chi = sv.chi;
+  c->lay[0] = sv.lay[0];
+  c->lay[1] = sv.lay[1];
+  c->lcur = sv.lcur;
+  c->rcur = sv.rcur;
+  c->oneq_done = sv.oneq_done;
+  c->plan_log.resize(sv.nplan);
+  c->stats.n_updates = sv.nupd;
+  c->projected = false;
+  return PC_OK;
+}
+
+// App. A.3: absorb the next layer of C_L and, from the same state, the next layer of C_R;
+// keep the one with the smaller size(M) (ties: left, as Algorithm 1 absorbs the left side
+// first).  When one side has no layer left the other is absorbed.  The one-qubit layer X^s
+// counts as the last layer of C_L.  Only the kept absorption stays in the plan and in
+// n_updates.
+pc_status absorb_step_adaptive(pc_circuit* c) {
+  const bool can_l = c->lcur < c->left_layers.size() || !c->oneq_done;
+  const bool can_r = c->rcur < c->right_layers.size();
+  if (!can_r) return absorb_left_layer(c);
+  if (!can_l) return absorb_right_layer(c);
+  pc_status st = save_state(c, 0);
+  if (st == PC_OK) st = absorb_left_layer(c);
+  if (st != PC_OK) return st;
+  const int64_t size_l = mpo_size(c);
+  st = save_state(c, 1);
+  if (st == PC_OK) st = load_state(c, 0);
+  if (st == PC_OK) st = absorb_right_layer(c);
+  if (st != PC_OK) return st;
+  if (size_l <= mpo_size(c)) st = load_state(c, 1);
+  if (st == PC_OK) CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
+  return st;
 }
 
 pc_status absorb_layer_pair(pc_circuit* c) {
@@ -1265,6 +1377,8 @@ void pc_default_config(pc_config* cfg) {
   cfg->device = 0;
   cfg->fp32_precondition = 1;
   cfg->precision = PC_PRECISION_FP64;
+  cfg->precondition_sweeps = 12;
+  cfg->side_mode = PC_SIDE_ALTERNATE;
 }
 
 pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
@@ -1272,7 +1386,8 @@ pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
   *out = nullptr;
   if (!(cfg->eps >= 0.0) || cfg->chi_max < 1 || cfg->chi_max > 1024 || !(cfg->tau > 0.0) ||
       cfg->max_unswap_iter < 0 || cfg->jacobi_max_sweeps < 1 || cfg->unswap_mode < 0 || cfg->unswap_mode > 2 ||
-      cfg->precision < PC_PRECISION_FP64 || cfg->precision > PC_PRECISION_TF32X3)
+      cfg->precision < PC_PRECISION_FP64 || cfg->precision > PC_PRECISION_TF32X3 || cfg->precondition_sweeps < 1 ||
+      cfg->side_mode < PC_SIDE_ALTERNATE || cfg->side_mode > PC_SIDE_ADAPTIVE)
     return PC_ERR_INVALID_ARG;
   auto* ctx = new pc_ctx();
   ctx->cfg = *cfg;
@@ -1345,6 +1460,7 @@ pc_status pc_load_gates(pc_ctx* ctx, int32_t n_qubits, int64_t n_gates, const in
   c->left_layers = make_layers(lorder, c->pairs.data(), n_qubits);
   c->right_layers = make_layers(rorder, c->pairs.data(), n_qubits);
   c->oneq_done = n_oneq == 0;
+  c->t_loaded = now_s();
   pc_status st = alloc_circuit(c);
   if (st != PC_OK) { free_circuit(c); return st; }
   st = reset_identity(c);
@@ -1377,13 +1493,15 @@ pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats
     // Algorithm 1: absorb layer pairs while size(M) < tau (progress rule: at least one)
     bool first = true;
     while ((first || (double)mpo_size(c) < tau) && layers_remain(c)) {
-      st = absorb_layer_pair(c);
+      st = ctx->cfg.side_mode == PC_SIDE_ADAPTIVE ? absorb_step_adaptive(c) : absorb_layer_pair(c);
       if (st != PC_OK) return st;
       first = false;
     }
+    trace_point(c, 0, 0);
     int acc = 0;
     st = unswap_stage(c, &acc);
     if (st != PC_OK) return st;
+    trace_point(c, 1, acc);
     if ((double)mpo_size(c) >= tau && layers_remain(c)) c->stats.stalled = 1;
     c->stats.n_stages += 1;
     c->stage += 1;
@@ -1403,6 +1521,19 @@ pc_status pc_contract(pc_circuit* c, pc_stats* stats) {
   if (st != PC_OK) return st;
   if (stats) *stats = local;
   return local.stalled ? PC_WARN_STALLED : PC_OK;
+}
+
+pc_status pc_get_trace(pc_circuit* c, int64_t cap, pc_trace_record* rec, int64_t* n_rec) {
+  if (check_circuit(c) != PC_OK || !n_rec || cap < 0) return PC_ERR_INVALID_ARG;
+  *n_rec = (int64_t)c->trace.size();
+  for (int64_t k = 0; rec && k < cap && k < *n_rec; ++k) rec[k] = c->trace[k];
+  return PC_OK;
+}
+
+pc_status pc_get_stats(pc_circuit* c, pc_stats* stats) {
+  if (check_circuit(c) != PC_OK || !stats) return PC_ERR_INVALID_ARG;
+  *stats = c->stats;
+  return PC_OK;
 }
 
 pc_status pc_get_cursors(pc_circuit* c, int64_t* left, int64_t* right) {

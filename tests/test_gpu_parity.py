@@ -154,6 +154,11 @@ def compare_runs(ref, c, circ, n_samples=40):
     u = mpo.uniforms(77, n_samples, n)
     samp_ref = mpo.sample(out, u)
     assert np.array_equal(c.sample(n_samples, 77), samp_ref)
+    # telemetry (Fig. 3 quantities): the same points as the oracle's trace
+    got_tr = [(r["stage"], r["phase"], r["gates"], r["size"], r["max_chi"], r["accepted"]) for r in c.trace()]
+    ref_tr = [(t["stage"], 0 if t["phase"] == "absorb" else 1, t["gates"], t["size"], t["max_chi"], t["accepted"])
+              for t in ref.trace]
+    assert got_tr == ref_tr
     xs = np.vstack([bits_ref[None], np.random.default_rng(0).integers(0, 2, (6, n)).astype(np.uint8)])
     amp_ref = mpo.amplitudes(out, xs)
     assert np.max(np.abs(c.amplitudes(xs) - amp_ref)) <= TOL_AMP
@@ -221,3 +226,17 @@ def test_errors_are_reported():
     with pytest.raises(binding.PcError) as e:
         c.apply_updates([1, 2], np.stack([np.eye(16)] * 2))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("n,eps_p,seed", [(8, 0.02, 2), (9, 0.03, 3)])
+def test_adaptive_side_selection_end_to_end(n, eps_p, seed):
+    """App. A.3: each absorption step keeps the side with the smaller size(M); the plans
+    (only the kept absorptions), unswap logs, layouts, spectra, peaks and samples must be the
+    oracle's."""
+    circ = W.hidden_permutation_mirror(n, 20, eps_p, seed=seed)
+    ref = mpo.contract(circ, mpo.Config(eps=1e-10, chi_max=64, tau=600, side_adaptive=True))
+    assert len(ref.sides) > 0
+    ctx = ctx_for(eps=1e-10, chi_max=64, tau=600, side_mode=binding.SIDE_ADAPTIVE)
+    c = ctx.load_circuit(circ)
+    c.contract()
+    compare_runs(ref, c, circ)

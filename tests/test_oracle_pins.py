@@ -305,3 +305,56 @@ def test_layers_are_disjoint_and_ordered():
             for q in c.pairs[g]:
                 seen_q[int(q)] = li
     assert sorted(g for layer in layers for g in layer) == list(range(c.n_gates))
+
+
+# --- App. A.3 adaptive side selection ---------------------------------------------------
+
+@pytest.mark.parametrize("seed,tau", [(3, 1e12), (4, 40)])
+def test_adaptive_order_keeps_the_circuit_operator(seed, tau):
+    """Left and right absorptions act on different legs and commute, so any absorption order
+    (here the adaptive one, with and without unswapping) ends at the circuit's operator."""
+    c = W.random_circuit(6, 16, seed=seed)
+    cfg = mpo.Config(eps=1e-14, chi_max=1 << 20, tau=tau, side_adaptive=True)
+    r = mpo.contract(c, cfg)
+    assert len(r.sides) > 0
+    op = sv.full_operator(c)
+    t_ref = sv.operator_to_sites(op, 6, r.layout_l.pos, r.layout_r.pos) / 2 ** 3
+    assert np.max(np.abs(dense_from_mpo(r.state) - t_ref)) < 1e-12
+    psi = sv.run_circuit(c)
+    bits, p, _, _ = mpo.extract_peak(mpo.project_zero(r))
+    assert to_index(bits) == int(np.argmax(np.abs(psi) ** 2))
+    assert abs(p - np.max(np.abs(psi) ** 2)) < 1e-12
+
+
+def test_adaptive_mirror_collapses_and_peaks_on_planted():
+    c = W.hidden_permutation_mirror(8, 16, 0.0, seed=2)
+    r = mpo.contract(c, mpo.Config(eps=1e-12, chi_max=64, tau=300, side_adaptive=True))
+    assert r.state.bond_dims() == [1] * 7
+    bits, p, _, _ = mpo.extract_peak(mpo.project_zero(r))
+    assert np.array_equal(bits, c.planted) and abs(p - 1.0) < 1e-12
+
+
+def test_adaptive_step_keeps_the_smaller_size():
+    """Each adaptive step leaves size(M) at the smaller of the two one-sided absorptions
+    (ties to the left), and the sides differ from plain alternation on this circuit."""
+    c = W.hidden_permutation_mirror(7, 14, 0.03, seed=5)
+    cfg = mpo.Config(eps=1e-10, chi_max=64, tau=1e12, side_adaptive=True, unswap_enabled=False)
+    ctr = mpo.Contraction(c, cfg)
+    sides = []
+    while ctr.layers_remain():
+        can_l = ctr.left_cursor < len(ctr.left_layers) or not ctr.oneq_done
+        can_r = ctr.right_cursor < len(ctr.right_layers)
+        sizes = {}
+        if can_l and can_r:
+            for side in (mpo.SIDE_LEFT, mpo.SIDE_RIGHT):
+                probe = mpo.Contraction(c, cfg)
+                probe._load(ctr._save())
+                (probe._absorb_left_layer if side == mpo.SIDE_LEFT else probe._absorb_right_layer)()
+                sizes[side] = probe.state.size()
+        side = ctr._absorb_step_adaptive()
+        sides.append(side)
+        if sizes:
+            assert ctr.state.size() == min(sizes.values())
+            assert side == (mpo.SIDE_LEFT if sizes[mpo.SIDE_LEFT] <= sizes[mpo.SIDE_RIGHT] else mpo.SIDE_RIGHT)
+    alternate = [mpo.SIDE_LEFT, mpo.SIDE_RIGHT] * len(sides)
+    assert sides != alternate[: len(sides)]
