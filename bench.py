@@ -248,7 +248,8 @@ def run_ours(args):
 
     seed = rank
     circ = W.workload_unswap28(seed)
-    ctx = binding.Context(eps=EPS, chi_max=CHI_MAX, tau=TAU, device=local)
+    extra = {"precondition_sweeps": args.pre_sweeps} if args.pre_sweeps > 0 else {}
+    ctx = binding.Context(eps=EPS, chi_max=CHI_MAX, tau=TAU, device=local, **extra)
     c = ctx.load_circuit(circ)
     B, lam = saturated_state(seed)
     c.set_state(B, lam)
@@ -375,6 +376,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-serving", action="store_true", help="skip the batching and serving measurements")
+    ap.add_argument("--pre-sweeps", type=int, default=0, help="FP32 preconditioning sweep cap (0: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -169,6 +169,16 @@ pc_status pc_set_cursors(pc_circuit* c, int64_t left, int64_t right);
 pc_status pc_snapshot(pc_circuit* c);
 pc_status pc_restore(pc_circuit* c);
 
+/* Host-file checkpoint of the contraction state: bond dimensions, site tensors, spectra,
+ * both layouts, both cursors, the one-qubit-layer flag and the stage counter (the MPO and
+ * the permutations P_L, P_R of Eq. 1 plus where the two fronts stand).  The gate list is not
+ * stored: pc_checkpoint_read restores into a circuit loaded with the same gates (same n and
+ * layer counts, checked) and chi_max at least the stored bond dimensions.  Binary format,
+ * little-endian, versioned; PC_ERR_INVALID_ARG for a file that does not match,
+ * PC_ERR_STATE for an unreadable / unwritable path. */
+pc_status pc_checkpoint_write(pc_circuit* c, const char* path);
+pc_status pc_checkpoint_read(pc_circuit* c, const char* path);
+
 /* One unswap stage (Sec. II.B.2) on the current MPO, in the configured mode.
  * *n_accepted (may be NULL) receives the number of accepted swaps. */
 pc_status pc_unswap(pc_circuit* c, int32_t* n_accepted);

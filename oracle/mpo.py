@@ -273,17 +273,17 @@ class Contraction:
         st = self.state
         return ([b.copy() for b in st.B], [l.copy() for l in st.lam],
                 {k: (list(v.pos), list(v.site)) for k, v in self.lay.items()},
-                self.left_cursor, self.right_cursor, self.oneq_done, len(self.res.plan), self.res.n_updates)
+                self.left_cursor, self.right_cursor, self.oneq_done, list(self.res.plan), self.res.n_updates)
 
     def _load(self, saved) -> None:
-        B, lam, lays, lc, rc, oq, nplan, nup = saved
+        B, lam, lays, lc, rc, oq, plan, nup = saved
         self.state.B = [b.copy() for b in B]
         self.state.lam = [l.copy() for l in lam]
         for k, (pos, site) in lays.items():
             self.lay[k].pos[:] = pos
             self.lay[k].site[:] = site
         self.left_cursor, self.right_cursor, self.oneq_done = lc, rc, oq
-        del self.res.plan[nplan:]
+        self.res.plan[:] = plan
         self.res.n_updates = nup
 
     def _absorb_step_adaptive(self) -> int:

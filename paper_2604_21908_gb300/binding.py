@@ -91,7 +91,7 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_get_bond_dims", "pc_get_layouts", "pc_get_spectrum", "pc_get_site", "pc_set_state",
            "pc_apply_updates", "pc_plan_routing", "pc_get_plan", "pc_get_unswap_log", "pc_kernel_timers",
            "pc_reset_kernel_timers", "pc_contract_iterations", "pc_get_cursors", "pc_set_cursors", "pc_snapshot",
-           "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_get_stats", "pc_get_trace", "pc_batch_create", "pc_batch_destroy",
+           "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_get_stats", "pc_get_trace", "pc_checkpoint_write", "pc_checkpoint_read", "pc_batch_create", "pc_batch_destroy",
            "pc_batch_attach", "pc_batch_detach", "pc_batch_contract", "pc_batch_counters", "pc_batch_set_timing",
            "pc_projected_bytes", "pc_server_create", "pc_server_submit", "pc_server_wait", "pc_server_get_stats",
            "pc_server_clock", "pc_server_destroy"]
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH):
         "pc_get_cursors": ([vp, _p(i64), _p(i64)], i32),
         "pc_get_stats": ([vp, _p(PcStats)], i32),
         "pc_get_trace": ([vp, i64, vp, _p(i64)], i32),
+        "pc_checkpoint_write": ([vp, C.c_char_p], i32),
+        "pc_checkpoint_read": ([vp, C.c_char_p], i32),
         "pc_set_cursors": ([vp, i64, i64], i32),
         "pc_snapshot": ([vp], i32),
         "pc_restore": ([vp], i32),
@@ -316,6 +318,12 @@ class Circuit:
         h = C.c_void_p()
         self._chk(self.lib.pc_get_stream(self.h, C.byref(h)), "pc_get_stream")
         return h.value or 0
+
+    def checkpoint_write(self, path: str):
+        self._chk(self.lib.pc_checkpoint_write(self.h, os.fsencode(path)), "pc_checkpoint_write")
+
+    def checkpoint_read(self, path: str):
+        self._chk(self.lib.pc_checkpoint_read(self.h, os.fsencode(path)), "pc_checkpoint_read")
 
     def snapshot(self):
         self._chk(self.lib.pc_snapshot(self.h), "pc_snapshot")

@@ -337,7 +337,7 @@ struct pc_circuit {
     Layout lay[2];
     size_t lcur = 0, rcur = 0;
     bool oneq_done = true;
-    size_t nplan = 0;
+    std::vector<std::array<int32_t, 5>> plan;
     int64_t nupd = 0;
   } saved[2];
 };
@@ -702,7 +702,12 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     int pre_sweeps = 1;
     for (int i = 0; i < P; ++i)
       pre_sweeps = std::max(pre_sweeps, flat[b0 + psub[i]].r->c->ctx->cfg.precondition_sweeps);
-    WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count, pl, ppairs, s));
+    if (pl <= 1024)
+      WS_TRY(pc::launch_jacobi32_blocked(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count,
+                                         pl, s));
+    else
+      WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count, pl,
+                                 ppairs, s));
     WS_TRY(pc::launch_widen_q(w->d_j32, w->d_q64, P, pv, s));
     for (int k = 0; k < 4; ++k) WS_TRY(pc::launch_gemm(w->d_ns + k * P, P, pv, pv, s));
     WS_TRY(pc::launch_gemm(w->d_ns + 4 * P, P, pv, pl, s));
@@ -1132,7 +1137,7 @@ pc_status save_state(pc_circuit* c, int k) {
   sv.lcur = c->lcur;
   sv.rcur = c->rcur;
   sv.oneq_done = c->oneq_done;
-  sv.nplan = c->plan_log.size();
+  sv.plan = c->plan_log;
   sv.nupd = c->stats.n_updates;
   return PC_OK;
 }
@@ -1148,7 +1153,7 @@ pc_status load_state(pc_circuit* c, int k) {
   c->lcur = sv.lcur;
   c->rcur = sv.rcur;
   c->oneq_done = sv.oneq_done;
-  c->plan_log.resize(sv.nplan);
+  c->plan_log = sv.plan;
   c->stats.n_updates = sv.nupd;
   c->projected = false;
   return PC_OK;
@@ -1586,6 +1591,107 @@ pc_status pc_restore(pc_circuit* c) {
   c->lcur = c->snap_lcur;
   c->rcur = c->snap_rcur;
   c->oneq_done = c->snap_oneq_done;
+  c->projected = false;
+  return PC_OK;
+}
+
+namespace {
+constexpr uint64_t kCkptMagic = 0x31544b4350434d50ull;   // "PMCPCKT1"
+
+bool write_all(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+bool read_all(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
+}  // namespace
+
+pc_status pc_checkpoint_write(pc_circuit* c, const char* path) {
+  if (check_circuit(c) != PC_OK || !path) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+  const int n = c->n;
+  std::vector<double2> sites;
+  for (int j = 0; j < n; ++j) {
+    const size_t cnt = (size_t)c->chi[j] * 4 * c->chi[j + 1];
+    const size_t o = sites.size();
+    sites.resize(o + cnt);
+    CUDA_TRY(ctx, cudaMemcpy(sites.data() + o, site_ptr(c, j), cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+  }
+  std::vector<double> lam;
+  for (int b = 0; b + 1 < n; ++b) {
+    const size_t o = lam.size();
+    lam.resize(o + c->chi[b + 1]);
+    CUDA_TRY(ctx, cudaMemcpy(lam.data() + o, lam_ptr(c, b), c->chi[b + 1] * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, PC_ERR_STATE, std::string("cannot write ") + path);
+  const int64_t hdr[8] = {(int64_t)kCkptMagic, n, (int64_t)c->left_layers.size(), (int64_t)c->right_layers.size(),
+                          (int64_t)c->lcur, (int64_t)c->rcur, c->oneq_done ? 1 : 0, c->stage};
+  bool ok = write_all(f, hdr, sizeof(hdr)) && write_all(f, c->chi.data(), (n + 1) * sizeof(int)) &&
+            write_all(f, c->lay[0].pos.data(), n * sizeof(int)) && write_all(f, c->lay[1].pos.data(), n * sizeof(int));
+  const int64_t ns = (int64_t)sites.size(), nl = (int64_t)lam.size();
+  ok = ok && write_all(f, &ns, sizeof(ns)) && write_all(f, sites.data(), sites.size() * sizeof(double2)) &&
+       write_all(f, &nl, sizeof(nl)) && write_all(f, lam.data(), lam.size() * sizeof(double));
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, PC_ERR_STATE, std::string("short write to ") + path);
+  return PC_OK;
+}
+
+pc_status pc_checkpoint_read(pc_circuit* c, const char* path) {
+  if (check_circuit(c) != PC_OK || !path) return PC_ERR_INVALID_ARG;
+  pc_ctx* ctx = c->ctx;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "cudaSetDevice");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, PC_ERR_STATE, std::string("cannot read ") + path);
+  const int n = c->n;
+  int64_t hdr[8];
+  std::vector<int> chi(n + 1), pos0(n), pos1(n);
+  int64_t ns = -1, nl = -1;
+  bool ok = read_all(f, hdr, sizeof(hdr)) && hdr[0] == (int64_t)kCkptMagic && hdr[1] == n &&
+            hdr[2] == (int64_t)c->left_layers.size() && hdr[3] == (int64_t)c->right_layers.size() &&
+            hdr[4] >= 0 && hdr[4] <= hdr[2] && hdr[5] >= 0 && hdr[5] <= hdr[3];
+  ok = ok && read_all(f, chi.data(), (n + 1) * sizeof(int)) && read_all(f, pos0.data(), n * sizeof(int)) &&
+       read_all(f, pos1.data(), n * sizeof(int));
+  // bond dimensions within the store, layouts permutations
+  if (ok) {
+    ok = chi[0] == 1 && chi[n] == 1;
+    for (int k = 1; ok && k < n; ++k) ok = chi[k] >= 1 && chi[k] <= c->cap[k];
+    std::vector<char> seen0(n, 0), seen1(n, 0);
+    for (int q = 0; ok && q < n; ++q) {
+      ok = pos0[q] >= 0 && pos0[q] < n && !seen0[pos0[q]] && pos1[q] >= 0 && pos1[q] < n && !seen1[pos1[q]];
+      if (ok) seen0[pos0[q]] = seen1[pos1[q]] = 1;
+    }
+  }
+  size_t want_s = 0, want_l = 0;
+  for (int j = 0; ok && j < n; ++j) want_s += (size_t)chi[j] * 4 * chi[j + 1];
+  for (int b = 0; ok && b + 1 < n; ++b) want_l += chi[b + 1];
+  std::vector<double2> sites;
+  std::vector<double> lam;
+  ok = ok && read_all(f, &ns, sizeof(ns)) && ns == (int64_t)want_s;
+  if (ok) { sites.resize(want_s); ok = read_all(f, sites.data(), want_s * sizeof(double2)); }
+  ok = ok && read_all(f, &nl, sizeof(nl)) && nl == (int64_t)want_l;
+  if (ok) { lam.resize(want_l); ok = read_all(f, lam.data(), want_l * sizeof(double)); }
+  std::fclose(f);
+  if (!ok) return fail(ctx, PC_ERR_INVALID_ARG, std::string("checkpoint does not match this circuit: ") + path);
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+  size_t so = 0, lo = 0;
+  for (int j = 0; j < n; ++j) {
+    const size_t cnt = (size_t)chi[j] * 4 * chi[j + 1];
+    CUDA_TRY(ctx, cudaMemcpy(site_ptr(c, j), sites.data() + so, cnt * sizeof(double2), cudaMemcpyHostToDevice));
+    so += cnt;
+  }
+  for (int b = 0; b + 1 < n; ++b) {
+    CUDA_TRY(ctx, cudaMemcpy(lam_ptr(c, b), lam.data() + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice));
+    lo += chi[b + 1];
+  }
+  c->chi = chi;
+  for (int side = 0; side < 2; ++side) {
+    const std::vector<int>& pos = side == 0 ? pos0 : pos1;
+    c->lay[side].pos = pos;
+    for (int q = 0; q < n; ++q) c->lay[side].site[pos[q]] = q;
+  }
+  c->lcur = (size_t)hdr[4];
+  c->rcur = (size_t)hdr[5];
+  c->oneq_done = hdr[6] != 0;
+  c->stage = (int)hdr[7];
   c->projected = false;
   return PC_OK;
 }

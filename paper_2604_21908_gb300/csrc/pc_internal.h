@@ -115,6 +115,12 @@ cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatu
 // stamp[k] = -1 for every row of every task (required before each Jacobi launch).
 cudaError_t launch_init_stamps(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 cudaError_t launch_init_stamps32(const JacobiTask32* d_tasks, int ntasks, int max_m, cudaStream_t stream);
+// The FP32 preconditioning sweeps in blocks of 8 rows (one block pair per CTA, rows in shared
+// memory, accumulator Q updated once per block pair).  Needs every task's row length
+// <= 1024 (returns cudaErrorInvalidValue otherwise: use launch_jacobi32) and stamp entries
+// for (m + 7) / 8 + 1 blocks set to -1; bar = 2 zeroed unsigned ints, err as launch_jacobi.
+cudaError_t launch_jacobi32_blocked(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                                    unsigned int* d_bar, int* d_err, int sm_count, int max_len, cudaStream_t stream);
 // Sets every task's accumulator Q (if any) to the identity.
 cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int max_m, cudaStream_t stream);
 // Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the

@@ -240,3 +240,34 @@ def test_adaptive_side_selection_end_to_end(n, eps_p, seed):
     c = ctx.load_circuit(circ)
     c.contract()
     compare_runs(ref, c, circ)
+
+
+def test_checkpoint_file_resume(tmp_path):
+    """Contract two outer iterations, write the state to a file, read it into a fresh circuit
+    with the same gates and finish there: bond dimensions, layouts, spectra and peak equal an
+    uninterrupted run's; a file for another circuit is rejected."""
+    circ = W.hidden_permutation_mirror(9, 24, 0.02, seed=6)
+    kw = dict(eps=1e-10, chi_max=64, tau=500)
+    ctx = ctx_for(**kw)
+    full = ctx.load_circuit(circ)
+    full.contract()
+    a = ctx.load_circuit(circ)
+    a.contract_iterations(2)
+    path = str(tmp_path / "state.ckpt")
+    a.checkpoint_write(path)
+    b = ctx.load_circuit(circ)
+    b.checkpoint_read(path)
+    assert b.cursors() == a.cursors()
+    assert list(b.bond_dims()) == list(a.bond_dims())
+    b.contract()
+    assert list(b.bond_dims()) == list(full.bond_dims())
+    assert [x.tolist() for x in b.layouts()] == [x.tolist() for x in full.layouts()]
+    for bond in range(circ.n_qubits - 1):
+        np.testing.assert_allclose(b.spectrum(bond), full.spectrum(bond), atol=TOL_SPEC, rtol=0)
+    bits_b, p_b, _ = b.extract_peak()
+    bits_f, p_f, _ = full.extract_peak()
+    assert np.array_equal(bits_b, bits_f) and abs(p_b - p_f) <= TOL_PEAK
+    other = ctx.load_circuit(W.hidden_permutation_mirror(8, 24, 0.02, seed=6))
+    with pytest.raises(binding.PcError) as e:
+        other.checkpoint_read(path)
+    assert e.value.status == -1

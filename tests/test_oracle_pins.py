@@ -358,3 +358,29 @@ def test_adaptive_step_keeps_the_smaller_size():
             assert side == (mpo.SIDE_LEFT if sizes[mpo.SIDE_LEFT] <= sizes[mpo.SIDE_RIGHT] else mpo.SIDE_RIGHT)
     alternate = [mpo.SIDE_LEFT, mpo.SIDE_RIGHT] * len(sides)
     assert sides != alternate[: len(sides)]
+
+
+def test_adaptive_plan_holds_the_kept_absorptions():
+    """The plan of an adaptive run, cut at the steps, replays to the same MPO: each step's
+    records are the updates of the side it kept (left = out-legs, right = in-legs)."""
+    c = W.hidden_permutation_mirror(7, 14, 0.03, seed=5)
+    cfg = mpo.Config(eps=1e-10, chi_max=64, tau=1e12, side_adaptive=True, unswap_enabled=False)
+    r = mpo.contract(c, cfg)
+    # replay: apply the recorded operators in order on a fresh identity MPO
+    st = mpo.MPOState(c.n_qubits)
+    lay = {mpo.SIDE_LEFT: mpo.Layout(c.n_qubits), mpo.SIDE_RIGHT: mpo.Layout(c.n_qubits)}
+    for rec in r.plan:
+        if rec.kind == 0:
+            st.apply(rec.bond, mpo.swap_operator(rec.side), cfg)
+            lay[rec.side].swap_sites(rec.bond)
+        else:
+            a, b = int(c.pairs[rec.gate, 0]), int(c.pairs[rec.gate, 1])
+            gate = c.mats[rec.gate]
+            if lay[rec.side].pos[a] > lay[rec.side].pos[b]:
+                gate = mpo.SWAP4 @ gate @ mpo.SWAP4
+            u16 = mpo.two_site_operator(gate, None) if rec.side == mpo.SIDE_LEFT else mpo.two_site_operator(None, gate)
+            st.apply(rec.bond, u16, cfg)
+    for q, g2 in zip(c.oneq_qubits, c.oneq_mats):
+        st.apply_one_site(lay[mpo.SIDE_LEFT].pos[int(q)], g2, mpo.SIDE_LEFT)
+    assert st.bond_dims() == r.state.bond_dims()
+    assert np.max(np.abs(dense_from_mpo(st) - dense_from_mpo(r.state))) < 1e-12
