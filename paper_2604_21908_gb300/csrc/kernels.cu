@@ -512,39 +512,47 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
 }
 
 // ---------------------------------------------------------------------------------------
-// Blocked FP32 Jacobi for the preconditioning sweeps.  The v rows of a task are cut into
-// blocks of BJ_BLOCK = 8 rows; the blocks are paired round-robin (NB - 1 block rounds per
-// sweep, one grid barrier each).  A CTA takes one block pair: its 16 rows go to shared
-// memory, one inner sweep rotates every pair of the 16 rows there (15 inner rounds of 8
-// pairs, two warps per pair), the rotations are accumulated into a 16 x 16 matrix W, and
-// the rows of X and of the accumulator Q are written back once (Q <- W Q).  Per pair of
-// rows this moves ~1/8 of the data of the row-pair kernel through L2.  Rotation rule, floors
-// and tolerance are the row-pair kernel's; norms are exact (recomputed from shared memory).
+// Blocked one-sided Jacobi (used for the FP32 preconditioning sweeps).  The v rows of a task
+// are cut into blocks of BLK = 8 rows; the blocks are paired round-robin (NB - 1 block rounds per sweep, one
+// grid barrier each).  A CTA takes one block pair: its 2 BLK rows go to shared memory (128 KB
+// at row length 1024), one inner sweep rotates every pair of them there
+// (2 BLK - 1 inner rounds of BLK pairs, two warps per pair), the rotations are accumulated
+// into a 2BLK x 2BLK matrix W, and the rows of X and of the accumulator Q (if any) are
+// written back once (Q <- W Q).  Per pair of rows this moves a fraction ~1/BLK of the data of
+// the row-pair kernel through L2 and needs one grid barrier per block round.  Rotation rule,
+// floors and tolerance are the row-pair kernel's; norms are exact (from shared memory).
 constexpr int BJ_THREADS = 512;
-constexpr int BJ_BLOCK = 8;
-constexpr int BJ_ROWS = 2 * BJ_BLOCK;
 constexpr int BJ_MAX_LEN = 1024;
 
-__global__ void __launch_bounds__(BJ_THREADS, 1) bjac32_kernel(const JacobiTask32* __restrict__ tasks, int ntasks,
-                                                               JacobiStatus* st, int max_sweeps,
-                                                               unsigned int* bar, int* err) {
-  extern __shared__ float2 bj_rows[];                      // [BJ_ROWS][Lmax]
-  __shared__ float2 W[BJ_ROWS][BJ_ROWS];
-  __shared__ float red[BJ_ROWS / 2][2][4];
+template <typename R> struct BjBlock;
+template <> struct BjBlock<float> { static constexpr int value = 8; };
+
+template <typename R>
+__global__ void __launch_bounds__(BJ_THREADS, 1) bjac_kernel(const typename JacTraits<R>::Task* __restrict__ tasks,
+                                                             int ntasks, JacobiStatus* st, int max_sweeps,
+                                                             unsigned int* bar, int* err) {
+  using C = typename JacTraits<R>::C;
+  using Task = typename JacTraits<R>::Task;
+  using Tr = JacTraits<R>;
+  constexpr int BJ_BLOCK = BjBlock<R>::value;
+  constexpr int BJ_ROWS = 2 * BJ_BLOCK;
+  extern __shared__ __align__(16) unsigned char bj_raw[];
+  C* bj_rows = reinterpret_cast<C*>(bj_raw);               // [BJ_ROWS][Lmax]
+  __shared__ C W[BJ_ROWS][BJ_ROWS];
+  __shared__ R red[BJ_ROWS / 2][2][4];
   __shared__ int s_grow[BJ_ROWS];
   __shared__ int s_nrot, s_skip;
   __shared__ int s_off[JAC_MAX_TASKS + 1];
   __shared__ int s_nbp[JAC_MAX_TASKS];
   __shared__ unsigned char s_done[JAC_MAX_TASKS];
-  __shared__ float s_dead2[JAC_MAX_TASKS], s_marg2[JAC_MAX_TASKS];
-  using Tr = JacTraits<float>;
+  __shared__ R s_dead2[JAC_MAX_TASKS], s_marg2[JAC_MAX_TASKS];
   for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
-    const JacobiTask32 tk = tasks[t];
+    const Task tk = tasks[t];
     const int nb = (tk.m + BJ_BLOCK - 1) / BJ_BLOCK;
     s_nbp[t] = nb + (nb & 1);
     s_done[t] = 0;
-    s_dead2[t] = tk.fro2 ? (float)(tk.dead_rel * *tk.fro2) : 0.0f;
-    s_marg2[t] = (float)(6 * tk.m) * s_dead2[t];
+    s_dead2[t] = tk.fro2 ? (R)(tk.dead_rel * *tk.fro2) : R(0);
+    s_marg2[t] = (R)(6 * tk.m) * s_dead2[t];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -586,7 +594,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac32_kernel(const JacobiTask3
       }
       const int t = lo;
       if (s_done[t]) continue;                             // uniform over the CTA
-      const JacobiTask32 tk = tasks[t];
+      const Task tk = tasks[t];
       const int Rb = s_nbp[t] - 1;
       const long long s = g / Rb;
       const int r = (int)(g - s * Rb);
@@ -609,31 +617,31 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac32_kernel(const JacobiTask3
         s_grow[threadIdx.x] = row < v ? row : -1;
       }
       for (int e = threadIdx.x; e < BJ_ROWS * BJ_ROWS; e += blockDim.x)
-        W[e / BJ_ROWS][e % BJ_ROWS] = make_float2((e / BJ_ROWS) == (e % BJ_ROWS) ? 1.0f : 0.0f, 0.0f);
+        W[e / BJ_ROWS][e % BJ_ROWS] = mk2((e / BJ_ROWS) == (e % BJ_ROWS) ? R(1) : R(0), R(0));
       __syncthreads();
       if (s_skip) { __syncthreads(); continue; }
       for (int e = threadIdx.x; e < BJ_ROWS * L; e += blockDim.x) {
         const int rr = e / L, k = e - rr * L;
         const int gr = s_grow[rr];
-        bj_rows[rr * L + k] = gr >= 0 ? __ldcg(tk.X + (size_t)gr * L + k) : make_float2(0.0f, 0.0f);
+        bj_rows[rr * L + k] = gr >= 0 ? __ldcg(tk.X + (size_t)gr * L + k) : mk2(R(0), R(0));
       }
       __syncthreads();
-      const float tol = 2.0f * Tr::eps * sqrtf((float)L);
-      const float dead2 = s_dead2[t], marg2 = s_marg2[t];
+      const R tol = R(2) * Tr::eps * sqrt((R)L);
+      const R dead2 = s_dead2[t], marg2 = s_marg2[t];
       for (int q = 0; q < BJ_ROWS - 1; ++q) {
         int ia, ib;
         if (pr == 0) { ia = BJ_ROWS - 1; ib = q; }
         else { ia = (q + pr) % (BJ_ROWS - 1); ib = (q - pr + BJ_ROWS - 1) % (BJ_ROWS - 1); }
-        if (s_grow[ia] >= 0 && s_grow[ib] >= 0) {          // uniform over the pair's 64 threads
-          float2* ra = bj_rows + ia * L;
-          float2* rb = bj_rows + ib * L;
-          float aa = 0.0f, bb = 0.0f, gr = 0.0f, gi = 0.0f;
+        if (pr < BJ_BLOCK && s_grow[ia] >= 0 && s_grow[ib] >= 0) {   // uniform over the pair's 64 threads
+          C* ra = bj_rows + ia * L;
+          C* rb = bj_rows + ib * L;
+          R aa = R(0), bb = R(0), gr = R(0), gi = R(0);
           for (int k = t64; k < L; k += 64) {
-            const float2 u = ra[k], w = rb[k];
-            aa = fmaf(u.x, u.x, fmaf(u.y, u.y, aa));
-            bb = fmaf(w.x, w.x, fmaf(w.y, w.y, bb));
-            gr = fmaf(u.x, w.x, fmaf(u.y, w.y, gr));
-            gi = fmaf(u.x, w.y, fmaf(-u.y, w.x, gi));
+            const C u = ra[k], w = rb[k];
+            aa = fma(u.x, u.x, fma(u.y, u.y, aa));
+            bb = fma(w.x, w.x, fma(w.y, w.y, bb));
+            gr = fma(u.x, w.x, fma(u.y, w.y, gr));
+            gi = fma(u.x, w.y, fma(-u.y, w.x, gi));
           }
           aa = warp_sum_t(aa); bb = warp_sum_t(bb); gr = warp_sum_t(gr); gi = warp_sum_t(gi);
           if (lane == 0) { red[pr][warp & 1][0] = aa; red[pr][warp & 1][1] = bb; red[pr][warp & 1][2] = gr; red[pr][warp & 1][3] = gi; }
@@ -643,30 +651,31 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac32_kernel(const JacobiTask3
           bb = red[pr][0][1] + red[pr][1][1];
           gr = red[pr][0][2] + red[pr][1][2];
           gi = red[pr][0][3] + red[pr][1][3];
-          const float g2 = fmaf(gr, gr, gi * gi);
-          const float lo2 = fminf(aa, bb), hi2 = fmaxf(aa, bb);
+          const R g2 = fma(gr, gr, gi * gi);
+          const R lo2 = fmin(aa, bb), hi2 = fmax(aa, bb);
           const bool rotate = !(aa < Tr::tiny || bb < Tr::tiny) && !(hi2 < dead2) && !(lo2 < dead2 && hi2 < marg2) &&
                               g2 >= Tr::g2min && (g2 > (tol * tol) * aa * bb);
           if (rotate) {
-            const float gabs = sqrtf(g2), inv_g = 1.0f / gabs;
-            const float zeta = 0.5f * (bb - aa) * inv_g;
-            float tt;
-            if (fabsf(zeta) > Tr::huge) tt = 0.5f / zeta;
-            else tt = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
-            Rot<float> rot;
-            rot.c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
+            const R gabs = sqrt(g2), inv_g = R(1) / gabs;
+            const R zeta = R(0.5) * (bb - aa) * inv_g;
+            R tt;
+            if (fabs(zeta) > Tr::huge) tt = R(0.5) / zeta;
+            else tt = copysign(R(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, R(1))));
+            Rot<R> rot;
+            // correctly rounded 1/sqrt (as in the row-pair kernel)
+            rot.c = R(1) / sqrt(fma(tt, tt, R(1)));
             rot.sn = rot.c * tt;
-            const float ex = gr * inv_g, ey = -gi * inv_g;
+            const R ex = gr * inv_g, ey = -gi * inv_g;
             rot.wx = rot.sn * ex; rot.wy = rot.sn * ey;
             rot.zx = rot.c * ex; rot.zy = rot.c * ey;
             for (int k = t64; k < L; k += 64) {
-              float2 u = ra[k], w = rb[k];
+              C u = ra[k], w = rb[k];
               rot_apply(rot, u, w);
               ra[k] = u;
               rb[k] = w;
             }
             if (t64 < BJ_ROWS) {
-              float2 u = W[ia][t64], w = W[ib][t64];
+              C u = W[ia][t64], w = W[ib][t64];
               rot_apply(rot, u, w);
               W[ia][t64] = u;
               W[ib][t64] = w;
@@ -683,20 +692,20 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac32_kernel(const JacobiTask3
           if (gr >= 0) tk.X[(size_t)gr * L + k] = bj_rows[rr * L + k];
         }
         // Q rows of the block pair <- W Q (columns split over the threads)
-        for (int cidx = threadIdx.x; cidx < v; cidx += blockDim.x) {
-          float2 qv[BJ_ROWS];
+        for (int cidx = threadIdx.x; tk.Q && cidx < v; cidx += blockDim.x) {
+          C qv[BJ_ROWS];
 #pragma unroll
           for (int rr = 0; rr < BJ_ROWS; ++rr)
-            qv[rr] = s_grow[rr] >= 0 ? __ldcg(tk.Q + (size_t)s_grow[rr] * v + cidx) : make_float2(0.0f, 0.0f);
+            qv[rr] = s_grow[rr] >= 0 ? __ldcg(tk.Q + (size_t)s_grow[rr] * v + cidx) : mk2(R(0), R(0));
 #pragma unroll
           for (int ii = 0; ii < BJ_ROWS; ++ii) {
             if (s_grow[ii] < 0) continue;
-            float2 acc = make_float2(0.0f, 0.0f);
+            C acc = mk2(R(0), R(0));
 #pragma unroll
             for (int rr = 0; rr < BJ_ROWS; ++rr) {
-              const float2 w = W[ii][rr];
-              acc.x = fmaf(w.x, qv[rr].x, fmaf(-w.y, qv[rr].y, acc.x));
-              acc.y = fmaf(w.x, qv[rr].y, fmaf(w.y, qv[rr].x, acc.y));
+              const C w = W[ii][rr];
+              acc.x = fma(w.x, qv[rr].x, fma(-w.y, qv[rr].y, acc.x));
+              acc.y = fma(w.x, qv[rr].y, fma(w.y, qv[rr].x, acc.y));
             }
             tk.Q[(size_t)s_grow[ii] * v + cidx] = acc;
           }
@@ -1091,24 +1100,33 @@ cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatu
                                 total_pairs, stream);
 }
 
-cudaError_t launch_jacobi32_blocked(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
-                                    unsigned int* d_bar, int* d_err, int sm_count, int max_len, cudaStream_t stream) {
+template <typename R>
+cudaError_t launch_bjac(const typename JacTraits<R>::Task* d_tasks, int ntasks, JacobiStatus* d_status,
+                        int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count, int max_len,
+                        cudaStream_t stream) {
+  using C = typename JacTraits<R>::C;
+  constexpr int rows = 2 * BjBlock<R>::value;
   if (ntasks <= 0) return cudaSuccess;
   if (ntasks > JAC_MAX_TASKS || max_len > BJ_MAX_LEN) return cudaErrorInvalidValue;
-  const int smem = BJ_ROWS * max_len * (int)sizeof(float2);
+  const int smem = rows * max_len * (int)sizeof(C);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bjac32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         BJ_ROWS * BJ_MAX_LEN * (int)sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(bjac_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         rows * BJ_MAX_LEN * (int)sizeof(C));
     if (e != cudaSuccess) return e;
     attr = true;
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bjac32_kernel, BJ_THREADS, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bjac_kernel<R>, BJ_THREADS, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   void* args[] = {(void*)&d_tasks, (void*)&ntasks, (void*)&d_status, (void*)&max_sweeps, (void*)&d_bar, (void*)&d_err};
-  return cudaLaunchCooperativeKernel((const void*)bjac32_kernel, dim3(sm_count), dim3(BJ_THREADS), args, smem, stream);
+  return cudaLaunchCooperativeKernel((const void*)bjac_kernel<R>, dim3(sm_count), dim3(BJ_THREADS), args, smem, stream);
+}
+
+cudaError_t launch_jacobi32_blocked(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
+                                    unsigned int* d_bar, int* d_err, int sm_count, int max_len, cudaStream_t stream) {
+  return launch_bjac<float>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, max_len, stream);
 }
 
 cudaError_t launch_precond_init(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m, int max_n,

@@ -654,9 +654,15 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
   // FP32 preconditioning of the tasks with enough vectors: FP32 sweeps with the rotations
   // accumulated in Q32; Q = polar(Q32) in FP64 by two Newton-Schulz steps
   // Q <- 1.5 Q - 0.5 (Q Q^H) Q; Y = Q X; then the FP64 sweeps run on Y.
+  // Each task's FP32 kernel is chosen by its own row length (blocked: rows in shared memory up
+  // to length 1024), so a task is factorised the same way alone and in any batch.
+  auto blocked32 = [&](int t) { return w->h_jt[t].n <= 1024; };
   std::vector<int> psub;
   for (int t = 0; t < T; ++t)
-    if (precond[t]) psub.push_back(t);
+    if (precond[t] && blocked32(t)) psub.push_back(t);
+  const int P32b = (int)psub.size();
+  for (int t = 0; t < T; ++t)
+    if (precond[t] && !blocked32(t)) psub.push_back(t);
   const int P = (int)psub.size();
   int pv = 0, pl = 0, ppairs = 0;
   for (int i = 0; i < P; ++i) {
@@ -702,12 +708,20 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     int pre_sweeps = 1;
     for (int i = 0; i < P; ++i)
       pre_sweeps = std::max(pre_sweeps, flat[b0 + psub[i]].r->c->ctx->cfg.precondition_sweeps);
-    if (pl <= 1024)
-      WS_TRY(pc::launch_jacobi32_blocked(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count,
-                                         pl, s));
-    else
-      WS_TRY(pc::launch_jacobi32(w->d_j32, P, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err, w->sm_count, pl,
-                                 ppairs, s));
+    int pl_b = 1, pl_e = 1, pairs_e = 0;
+    for (int i = 0; i < P; ++i) {
+      const pc::JacobiTask& jt = w->h_jt[psub[i]];
+      if (i < P32b) pl_b = std::max(pl_b, jt.n);
+      else { pl_e = std::max(pl_e, jt.n); pairs_e += jt.mp / 2; }
+    }
+    if (P32b > 0)
+      WS_TRY(pc::launch_jacobi32_blocked(w->d_j32, P32b, w->d_jst + w->cap, pre_sweeps, w->d_bar, w->d_err,
+                                         w->sm_count, pl_b, s));
+    if (P > P32b) {
+      WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+      WS_TRY(pc::launch_jacobi32(w->d_j32 + P32b, P - P32b, w->d_jst + w->cap + P32b, pre_sweeps, w->d_bar, w->d_err,
+                                 w->sm_count, pl_e, pairs_e, s));
+    }
     WS_TRY(pc::launch_widen_q(w->d_j32, w->d_q64, P, pv, s));
     for (int k = 0; k < 4; ++k) WS_TRY(pc::launch_gemm(w->d_ns + k * P, P, pv, pv, s));
     WS_TRY(pc::launch_gemm(w->d_ns + 4 * P, P, pv, pl, s));
@@ -725,6 +739,8 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
   int max_sweeps = 1;
   for (int t = 0; t < T; ++t) max_sweeps = std::max(max_sweeps, flat[b0 + t].r->c->ctx->cfg.jacobi_max_sweeps);
   WS_TRY(pc::launch_init_stamps(w->d_jy, T, max_v, s));
+  // FP64 sweeps: the row-pair kernel (FP64-pipe bound; a blocked variant with rows in shared
+  // memory measured slower: its exact per-pair norms double the FP64 work of a check)
   WS_TRY(pc::launch_jacobi(w->d_jy, T, w->d_jst, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_len, total_pairs, s));
   w->t_launch[1] += 1;
   timer_mark(w, 2);
@@ -742,6 +758,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     pc_circuit* c = flat[b0 + psub[i]].r->c;
     c->stats.max_sweeps_fp32 = std::max(c->stats.max_sweeps_fp32, w->h_jst[w->cap + i].sweeps);
   }
+
   if (w->timing) {
     float a = 0, b = 0, d = 0;
     cudaEventElapsedTime(&a, w->ev[0], w->ev[1]);
@@ -1382,7 +1399,7 @@ void pc_default_config(pc_config* cfg) {
   cfg->device = 0;
   cfg->fp32_precondition = 1;
   cfg->precision = PC_PRECISION_FP64;
-  cfg->precondition_sweeps = 12;
+  cfg->precondition_sweeps = 20;
   cfg->side_mode = PC_SIDE_ALTERNATE;
 }
 
