@@ -41,6 +41,7 @@ N_QUBITS, CHI_MAX, EPS, TAU = 28, 256, 1e-10, 1e6
 CURSOR = 12
 N_SAMPLES = 1000
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+JACOBI64_DRAM_BYTES = 1.50e9 + 66.38e9             # ncu: one FP64 Jacobi launch, four chi=256 updates
 
 
 def workload_name():
@@ -103,6 +104,20 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def aggregate_over_ranks(dev_ms: float, units: int, dist, device) -> tuple[float, int]:
+    """Whole-job figures over the ranks: the slowest rank's device time (MAX) and the units
+    all ranks processed (SUM).  Replicas share nothing else: no collective touches the data
+    path.  `device` is where the reduction tensors live (cuda for NCCL, cpu for gloo)."""
+    if dist is None:
+        return dev_ms, units
+    import torch
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
 
 
 def dist_setup():
@@ -290,15 +305,7 @@ def run_ours(args):
     launches, kms, kflops = c.timers()
     clk = clocks.stop()
     c.reset_timers(False)
-    t_max = dev_ms
-    units_all = units
-    if dist:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([units], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units_all = int(u.item())
+    t_max, units_all = aggregate_over_ranks(dev_ms, units, dist, "cuda")
     value = units_all / (t_max / 1e3)
 
     # end to end through the public API with host buffers: load the gate list, upload the
@@ -342,9 +349,13 @@ def run_ours(args):
                               "fallbacks": stats["fallbacks"]},
             "peak_probability": p,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "jacobi_kernel (FP64 one-sided Jacobi factorisation)",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": JACOBI64_DRAM_BYTES,
+                         "kernel": "bond factorisation phase of a wave: blocked FP32 preconditioning sweeps, "
+                                   "FP64 polar GEMMs and the FP64 jacobi_kernel (the dominant kernel)",
                          "flops_per_launch": jac_flops, "ms_per_launch": jac_ms,
+                         "traffic_note": "dram read+write of one FP64 jacobi_kernel launch on four chi=256 "
+                                         "updates (ncu, profiles/jacobi_kernel_dram_chi256_batch4.md); the "
+                                         "bench's waves average 4.7 such updates",
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 pipe)"},
             "kernel_share": {name: {"launches": int(launches[k]), "ms": float(kms[k]), "tflops": float(kflops[k] / 1e12)}
                              for k, name in enumerate(["merge_gate", "jacobi", "truncate", "split", "other"])},
