@@ -271,3 +271,20 @@ def test_checkpoint_file_resume(tmp_path):
     with pytest.raises(binding.PcError) as e:
         other.checkpoint_read(path)
     assert e.value.status == -1
+
+
+def test_failure_statuses_without_a_fault():
+    """Failure detection through status codes, no GPU fault involved: a Jacobi sweep cap of 1
+    cannot orthogonalise a random bond matrix (PC_ERR_NOCONVERGE); a circuit with no mirror
+    structure keeps size(M) above a tiny tau after unswapping, so the contraction finishes with
+    PC_WARN_STALLED (Sec. III.A) exactly where the oracle stalls, with the oracle's result."""
+    ctx = ctx_for(eps=1e-10, chi_max=64, jacobi_max_sweeps=1, fp32_precondition=0)
+    c = ctx.load_circuit(W.random_circuit(6, 12, seed=1))
+    with pytest.raises(binding.PcError) as e:
+        c.contract()
+    assert e.value.status == -4
+    circ = W.random_circuit(6, 20, seed=2)
+    ref, ctx2, c2, stats = run_both(circ, eps=1e-10, chi_max=64, tau=50)
+    assert ref.stalled
+    assert stats["status"] == 1 and stats["stalled"] == 1
+    compare_runs(ref, c2, circ)
