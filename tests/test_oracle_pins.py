@@ -384,3 +384,34 @@ def test_adaptive_plan_holds_the_kept_absorptions():
         st.apply_one_site(lay[mpo.SIDE_LEFT].pos[int(q)], g2, mpo.SIDE_LEFT)
     assert st.bond_dims() == r.state.bond_dims()
     assert np.max(np.abs(dense_from_mpo(st) - dense_from_mpo(r.state))) < 1e-12
+
+
+def test_best_first_peak_equals_exhaustive_argmax_n12():
+    """Best-first search over prefix marginals returns the exhaustive argmax of |<x|C|0>|^2
+    (here a strongly perturbed 12-qubit mirror whose peak is far below 1)."""
+    c = W.hidden_permutation_mirror(12, 6, 0.5, seed=8)
+    r = mpo.contract(c, mpo.Config(eps=1e-13, chi_max=4096, tau=1e12))
+    m = mpo.project_zero(r)
+    psi = sv.run_circuit(c)
+    probs = np.abs(psi) ** 2
+    bits, p, _, _ = mpo.extract_peak(m)
+    assert to_index(bits) == int(np.argmax(probs))
+    assert abs(p - probs.max()) < 1e-12
+    assert probs.max() < 0.9
+
+
+def test_input_side_permutation_changes_no_amplitude():
+    """P_R acts on |0...0> first and P|0...0> = |0...0>: a SWAP network placed before a circuit
+    (the outermost part of C_R) leaves every amplitude of C|0> unchanged (Eq. 1)."""
+    base = W.random_circuit(6, 12, seed=9)
+    rng = np.random.default_rng(3)
+    swaps = [tuple(int(q) for q in rng.choice(6, 2, replace=False)) for _ in range(5)]
+    pairs = np.vstack([np.array(swaps, np.int32), base.pairs])
+    mats = np.concatenate([np.stack([mpo.SWAP4] * len(swaps)), base.mats])
+    pre = W.Circuit(6, pairs, mats, base.split_index + len(swaps), base.oneq_qubits, base.oneq_mats)
+    amps = []
+    for c in (base, pre):
+        r = mpo.contract(c, mpo.Config(eps=1e-14, chi_max=1 << 20, tau=30))
+        amps.append(mpo.amplitudes(mpo.project_zero(r), all_bits(6)))
+    assert np.max(np.abs(amps[0] - amps[1])) < 1e-12
+    assert np.max(np.abs(amps[0] - sv.run_circuit(base))) < 1e-12
