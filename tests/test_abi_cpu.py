@@ -60,3 +60,40 @@ def test_plan_routing_rejects_bad_pairs():
         binding.plan_routing(4, np.array([[0, 0]]), 0)
     with pytest.raises(binding.PcError):
         binding.plan_routing(4, np.array([[0, 4]]), 0)
+
+
+def test_projected_bytes_matches_its_definition():
+    """pc_projected_bytes (host-only): site store at the bond capacities (1 at the ends, chi_max
+    inside), spectra, right environments plus one chi_max^2 scratch, the peak-search pool of 4096
+    vectors and five buffers per sample (at most 4096 samples at a time), in complex doubles."""
+    def expected(n, chi, s):
+        cap = [1] + [chi] * (n - 1) + [1]
+        sites = sum(cap[j] * 4 * cap[j + 1] for j in range(n)) * 16
+        env = sum(cap[j] * cap[j] for j in range(n)) * 16
+        return sites + max(1, n - 1) * chi * 8 + env + chi * chi * 16 + 4096 * chi * 16 + min(s, 4096) * chi * 5 * 16
+
+    for n, chi, s in [(2, 1, 0), (8, 64, 0), (28, 256, 1000), (56, 1024, 10000)]:
+        assert binding.projected_bytes(n, chi, s) == expected(n, chi, s)
+    assert binding.projected_bytes(28, 512, 0) > binding.projected_bytes(28, 256, 0)
+    assert binding.load().pc_projected_bytes(1, 64, 0) == -1
+    assert binding.load().pc_projected_bytes(8, 0, 0) == -1
+
+
+def test_config_validation_and_no_gpu_fails_loudly():
+    """Out-of-range settings are rejected before any device call; without a GPU, creating a
+    context fails with PC_ERR_CUDA (there is no CPU fallback)."""
+    import ctypes as C
+
+    import torch
+
+    lib = binding.load()
+    h = C.c_void_p()
+    for bad in (dict(chi_max=0), dict(chi_max=2048), dict(eps=-1.0), dict(tau=0.0), dict(unswap_mode=3),
+                dict(precision=2), dict(side_mode=2), dict(precondition_sweeps=0), dict(jacobi_max_sweeps=0)):
+        cfg = binding.default_config(**bad)
+        assert lib.pc_create(C.byref(cfg), C.byref(h)) == -1, bad
+    if not torch.cuda.is_available():
+        cfg = binding.default_config()
+        assert lib.pc_create(C.byref(cfg), C.byref(h)) == -7
+        with pytest.raises(binding.PcError):
+            binding.Server(max_resident=1, memory_budget=1 << 20)
