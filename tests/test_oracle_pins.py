@@ -415,3 +415,22 @@ def test_input_side_permutation_changes_no_amplitude():
         amps.append(mpo.amplitudes(mpo.project_zero(r), all_bits(6)))
     assert np.max(np.abs(amps[0] - amps[1])) < 1e-12
     assert np.max(np.abs(amps[0] - sv.run_circuit(base))) < 1e-12
+
+
+@pytest.mark.parametrize("parallel", [True, False])
+def test_unswapped_layouts_reproduce_the_permutation(parallel):
+    """Eq. 1 on a permutation-only circuit C = X^s P_pi: once every bond is at dimension 1 the
+    whole permutation sits in the layouts.  A basis state with a single 1 on input qubit q
+    enters at site layout_R[q] and leaves from the qubit the left layout puts at that site; the
+    statevector of C (without the X^s layer) says where that 1 goes."""
+    c = W.permutation_only(8, seed=5, planted=False)
+    r = mpo.contract(c, mpo.Config(eps=1e-12, chi_max=256, tau=100, unswap_parallel=parallel))
+    assert r.state.bond_dims() == [1] * 7
+    site_to_out = {s: q for q, s in enumerate(r.layout_l.pos)}
+    for q in range(8):
+        psi0 = np.zeros(2 ** 8, np.complex128)
+        psi0[1 << q] = 1.0
+        psi = sv.run_circuit(c, psi0)
+        out = int(np.argmax(np.abs(psi)))
+        assert abs(abs(psi[out]) - 1.0) < 1e-12
+        assert out == 1 << site_to_out[r.layout_r.pos[q]]
