@@ -8,7 +8,8 @@ implementations of the same method, compared element by element in the parity te
 Modules:
   mpo         -- the algorithm of the paper (Algorithm 1; Sec. II.B absorption, unswapping,
                  rewiring; Sec. II.C sampling; App. A.1 parallel swap selection; App. A.2
-                 non-strict acceptance) in plain numpy/scipy FP64, in the paper's order.
+                 non-strict acceptance; App. A.3 adaptive side selection; the Fig. 3
+                 telemetry) in plain numpy/scipy FP64, in the paper's order.
   statevector -- brute-force statevector / full-operator simulation used to pin the oracle.
 
 Every function is pinned by tests under ``tests/`` against closed forms, brute force or

@@ -334,7 +334,12 @@ class Contraction:
         """App. A.1: for each (side, parity) in the fixed order, try the swap on every bond
         of that parity at once (the bonds are disjoint, so every trial reads the pre-batch
         state), keep those that reduce the bond dimension; stop after a full cycle with no
-        reduction or after max_unswap_iter cycles."""
+        reduction or after max_unswap_iter cycles.
+
+        Pinned: trial counts equal brute-force operator-Schmidt ranks, strict acceptance lowers
+        the total bond dimension, permutation-only circuits end at dimension 1 with the
+        permutation in the layouts, the operator is unchanged.  The accepted sequence on
+        perturbed circuits: parity unpinned (no closed form; compared with the GPU only)."""
         st = self.state
         accepted_total = 0
         for it in range(self.cfg.max_unswap_iter):
@@ -359,7 +364,10 @@ class Contraction:
     def unswap_sequential(self) -> int:
         """Algorithm 1 unswapping: take the available bond with the largest dimension
         (smallest index on ties), try left, right and both; accept the smallest resulting
-        dimension (ties in that side order) if it reduces the bond; update the available set."""
+        dimension (ties in that side order) if it reduces the bond; update the available set.
+
+        Pinned on permutation-only circuits (dimension 1, permutation in the layouts); the
+        accepted sequence on perturbed circuits: parity unpinned, as for the parallel variant."""
         st = self.state
         avail = set(range(self.n - 1))
         accepted_total = 0
