@@ -366,8 +366,11 @@ class Contraction:
         (smallest index on ties), try left, right and both; accept the smallest resulting
         dimension (ties in that side order) if it reduces the bond; update the available set.
 
-        Pinned on permutation-only circuits (dimension 1, permutation in the layouts); the
-        accepted sequence on perturbed circuits: parity unpinned, as for the parallel variant."""
+        Pinned on permutation-only circuits (dimension 1, permutation in the layouts) and, for
+        N <= 6, step by step against a replay of this selection rule on the dense operator from
+        the statevector simulator (bond, side, acceptance, layouts, final operator).  The
+        accepted sequence on perturbed circuits at scale: parity unpinned, as for the parallel
+        variant."""
         st = self.state
         avail = set(range(self.n - 1))
         accepted_total = 0
@@ -396,7 +399,9 @@ class Contraction:
     def run(self) -> Result:
         """Algorithm 1 main loop.  Reading for the stall case (Sec. III.A notes the method
         can stall): each outer iteration absorbs at least one layer pair; if size(M) is still
-        >= tau after unswapping, the result is flagged stalled."""
+        >= tau after unswapping, the result is flagged stalled.  Pinned on circuits whose size
+        after each stage is fixed by construction (stalled, not stalled because nothing is left,
+        not stalled because unswapping brought the size under tau)."""
         st, cfg = self.state, self.cfg
         while self.layers_remain():
             first = True
@@ -506,7 +511,9 @@ def extract_peak(mps: OutputMPS, max_expansions: int = 200000):
 
 def splitmix64(seed: int, counter: int) -> int:
     """SplitMix64 (Steele, Lea, Flood 2014; Vigna's public-domain reference) evaluated at
-    state seed + (counter + 1) * golden-gamma, as a counter-based generator."""
+    state seed + (counter + 1) * golden-gamma, as a counter-based generator.  Pinned to the
+    generator's published outputs (first five from seed 1234567; bucket counts from seed
+    987654321)."""
     m = (1 << 64) - 1
     z = (seed + (counter + 1) * 0x9E3779B97F4A7C15) & m
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
