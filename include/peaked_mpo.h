@@ -258,12 +258,13 @@ pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
  *   s_dev   DEVICE float64[min(m, n, chi_max)]: kept singular values, normalised to unit 2-norm
  *   vh_dev  DEVICE float64[min(m, n, chi_max)][n][2]: kept right singular vectors as rows
  *   count   HOST: number of values kept
- *   stream  a cudaStream_t, or NULL for the default stream; the call returns after it
- *           has synchronised that stream.
+ *   stream  a cudaStream_t, or NULL for the default stream; the call is synchronous: it
+ *           copies the count back and returns after it has synchronised that stream.
  * Sizes beyond 256 return PC_ERR_INVALID_ARG.  Every call shares the one array and leaves
  * its contents there; calls that overlap on the GPU (concurrent streams, threads) race.
  * The first call on a device looks up the array's address with that device current:
- * make it before any stream capture. */
+ * make it before any stream capture.  The address is cached per device for the life of
+ * the process and is stale after a cudaDeviceReset of that device. */
 pc_status pc_factorise_noalloc(const double* x_dev, int32_t m, int32_t n, double eps, int32_t chi_max,
                                double* s_dev, double* vh_dev, int32_t* count, void* stream);
 

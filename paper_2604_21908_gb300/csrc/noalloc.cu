@@ -13,7 +13,12 @@
 //   - every GPU that loads the library holds the array (about 2.1 MB) until the process exits;
 //   - every call on a device shares the array; calls that overlap on the GPU race;
 //   - the first call on a device resolves the array's device address (cudaGetSymbolAddress
-//     with that device current); make that first call before any stream capture.
+//     with that device current); make that first call before any stream capture;
+//   - the call is synchronous: it reads the kept count back and synchronises the stream
+//     before it returns;
+//   - the resolved address is cached per device for the life of the process; after a
+//     cudaDeviceReset of that device it is stale, so do not call this entry point again
+//     in a process that reset the device.
 #include "../../include/peaked_mpo.h"
 #include "pc_internal.h"
 

@@ -3,7 +3,9 @@ cudaMalloc, checked against the library's regular two-site update (pc_apply_upda
 same bond matrices: same count, spectra within TOL_SPEC, and the same kept right singular
 subspace (its projector, which does not depend on the phase of each vector) within TOL_AMP.
 Two different matrices (a wide one, factorised through its rows, and a tall one, through
-its columns) and the first again, in a row, so the shared scratch is reused."""
+its columns) and the first again, in a row, so the shared scratch is reused.  Further shapes
+(odd, single row or column, the 256 x 256 limit, cutoff active) against numpy's SVD, and a
+check that repeated calls allocate no device memory."""
 import numpy as np
 import pytest
 
@@ -69,6 +71,75 @@ def test_noalloc_factorisation_matches_regular_update():
         assert np.max(np.abs(vh @ vh.conj().T - np.eye(k))) < TOL_AMP
         proj, proj_ref = vh.conj().T @ vh, ref_vh.conj().T @ ref_vh
         assert np.max(np.abs(proj - proj_ref)) < TOL_AMP
+
+
+def _factorise(x, eps, chi_max):
+    import torch
+    m, n = x.shape
+    dev = torch.device("cuda")
+    xt = torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag], -1))).to(dev)
+    kmax = min(m, n, chi_max)
+    s_out = torch.zeros(kmax, dtype=torch.float64, device=dev)
+    vh_out = torch.zeros(kmax, n, 2, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    k = binding.factorise_noalloc(xt.data_ptr(), m, n, eps, chi_max, s_out.data_ptr(), vh_out.data_ptr())
+    s = s_out.cpu().numpy()[:k]
+    vh = vh_out.cpu().numpy()[:k]
+    return k, s, vh[..., 0] + 1j * vh[..., 1]
+
+
+def _matrix(m, n, seed, decay):
+    """m x n complex matrix with singular values exp(-decay k), random singular vectors."""
+    rng = np.random.default_rng(seed)
+    r = min(m, n)
+    u, _ = np.linalg.qr(rng.standard_normal((m, r)) + 1j * rng.standard_normal((m, r)))
+    v, _ = np.linalg.qr(rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r)))
+    s = np.exp(-decay * np.arange(r))
+    return (u * s[None, :]) @ v.conj().T
+
+
+@pytest.mark.parametrize("m,n,decay,chi_max", [
+    (7, 33, 0.5, 64),       # odd row count: the Jacobi pads one row
+    (33, 7, 0.5, 64),       # tall: factorised through its 7 columns
+    (1, 5, 0.0, 8),         # a single row
+    (5, 1, 0.0, 8),         # a single column
+    (256, 256, 0.2, 64),    # the size limit, widest Jacobi group, cap active
+    (200, 120, 0.25, 256),  # cutoff active: exp(-0.25 k) crosses 1e-10 between k = 92 and 93
+])
+def test_noalloc_shapes_against_numpy_svd(m, n, decay, chi_max):
+    """Count, kept spectrum and the kept right singular subspace against numpy's SVD of the
+    same matrix under the same rule (keep s_k > eps s_0, at least 1, at most chi_max,
+    renormalise to unit 2-norm)."""
+    eps = 1e-10
+    x = _matrix(m, n, seed=m * 1000 + n, decay=decay)
+    _, s_ref, vh_ref = np.linalg.svd(x, full_matrices=False)
+    k_ref = max(1, min(int(np.sum(s_ref > eps * s_ref[0])), chi_max))
+    k, s, vh = _factorise(x, eps, chi_max)
+    assert k == k_ref
+    np.testing.assert_allclose(s, s_ref[:k] / np.linalg.norm(s_ref[:k]), atol=TOL_SPEC, rtol=0)
+    assert np.max(np.abs(vh @ vh.conj().T - np.eye(k))) < TOL_AMP
+    proj, proj_ref = vh.conj().T @ vh, vh_ref[:k].conj().T @ vh_ref[:k]
+    assert np.max(np.abs(proj - proj_ref)) < 1e-9
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call (which resolves the scratch array's address and loads the kernels)
+    repeated calls change neither the device memory torch has allocated nor the device's
+    free memory."""
+    import torch
+    x = _matrix(96, 80, seed=5, decay=0.1)
+    dev = torch.device("cuda")
+    xt = torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag], -1))).to(dev)
+    s_out = torch.zeros(64, dtype=torch.float64, device=dev)
+    vh_out = torch.zeros(64, 80, 2, dtype=torch.float64, device=dev)
+    binding.factorise_noalloc(xt.data_ptr(), 96, 80, 1e-10, 64, s_out.data_ptr(), vh_out.data_ptr())
+    torch.cuda.synchronize()
+    free1, alloc1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):
+        binding.factorise_noalloc(xt.data_ptr(), 96, 80, 1e-10, 64, s_out.data_ptr(), vh_out.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc1
+    assert torch.cuda.mem_get_info()[0] == free1
 
 
 def test_noalloc_rejects_sizes_beyond_the_limit():
