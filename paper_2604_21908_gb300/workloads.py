@@ -200,6 +200,95 @@ def hidden_permutation_mirror(n: int, gates_per_half: int, eps_pert: float, seed
                     "eps_pert": eps_pert, "seed": seed, "n_perm_gates": len(p_pairs)})
 
 
+def rzz(theta: float) -> np.ndarray:
+    """RZZ(theta) = exp(-i theta/2 Z(x)Z), the trapped-ion native two-qubit gate."""
+    a = np.exp(-0.5j * theta)
+    return np.diag([a, np.conj(a), np.conj(a), a]).astype(np.complex128)
+
+
+def haar_su2(rng: np.random.Generator) -> np.ndarray:
+    u = haar_unitary(rng, 2)
+    return u / np.sqrt(np.linalg.det(u))
+
+
+_H2 = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2.0)
+_SDG = np.diag([1.0, -1.0j]).astype(np.complex128)
+_I2 = np.eye(2, dtype=np.complex128)
+
+
+def _cnot_from_rzz(control_first: bool) -> np.ndarray:
+    """CNOT written in the native set: CZ = e^{i pi/4} (S^dagger (x) S^dagger) RZZ(pi/2), with
+    Hadamards on the target."""
+    cz = np.exp(0.25j * np.pi) * np.kron(_SDG, _SDG) @ rzz(0.5 * np.pi)
+    h = np.kron(_I2, _H2) if control_first else np.kron(_H2, _I2)
+    return h @ cz @ h
+
+
+def swap_as_native_gates(rng: np.random.Generator) -> list[np.ndarray]:
+    """A SWAP as three two-qubit gates, each one RZZ(pi/2) dressed with one-qubit gates:
+    CNOT(a->b) CNOT(b->a) CNOT(a->b) with random SU(2) pairs inserted between them and undone
+    in the next gate, so no gate looks like a SWAP or a CNOT.  The product (time order g1, g2,
+    g3) is exactly SWAP."""
+    c_ab, c_ba = _cnot_from_rzz(True), _cnot_from_rzz(False)
+    r1 = np.kron(haar_su2(rng), haar_su2(rng))
+    r2 = np.kron(haar_su2(rng), haar_su2(rng))
+    return [r1 @ c_ab, r2 @ c_ba @ r1.conj().T, c_ab @ r2.conj().T]
+
+
+def hqap_like_mirror(n: int, rzz_per_half: int, n_swaps: int, angle_noise: float, seed: int = 0) -> Circuit:
+    """A peaked circuit shaped like the HQAP construction the paper attacks (Sec. I, Sec. III:
+    RZZ two-qubit gates with one-qubit layers, a U U^dagger mirror, swap insertions, angle
+    sweeping, a planted bitstring).  Synthetic: nothing here reconstructs the paper's circuit.
+
+    * U: layers of RZZ(theta) gates on random perfect matchings of the qubits (all-to-all, as on
+      a trapped-ion machine), each preceded by Haar SU(2) gates on its two qubits (the one-qubit
+      layers, fused into the two-qubit gate); theta uniform in [0.2, pi - 0.2].
+    * Swap insertion: a permutation pi made of `n_swaps` transpositions of random qubit pairs,
+      each SWAP written as three RZZ-native gates (`swap_as_native_gates`).
+    * The mirrored half V^dagger with V = P_pi U P_pi^dagger: U's gates in reverse order,
+      relabelled by pi, each inverted with its RZZ angle swept by a Gaussian offset of standard
+      deviation `angle_noise` (the peak weight falls roughly as exp(-rzz_per_half
+      angle_noise^2 / 4)).
+    * X^s: the planted bitstring, last in time.
+    The gate list is two-qubit 4x4 matrices (one-qubit gates fused) plus the final X layer."""
+    rng = rng_for(15, seed)
+    u_pairs, u_mats, u_parts = [], [], []
+    while len(u_pairs) < rzz_per_half:
+        order = rng.permutation(n)
+        for k in range(0, n - 1, 2):
+            if len(u_pairs) == rzz_per_half:
+                break
+            a, b = int(order[k]), int(order[k + 1])
+            theta = float(rng.uniform(0.2, np.pi - 0.2))
+            dress = np.kron(haar_su2(rng), haar_su2(rng))
+            u_pairs.append((a, b))
+            u_mats.append(rzz(theta) @ dress)
+            u_parts.append((theta, dress))
+    perm = np.arange(n, dtype=np.int32)
+    p_pairs, p_mats = [], []
+    for _ in range(n_swaps):
+        a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+        for g in swap_as_native_gates(rng):
+            p_pairs.append((a, b))
+            p_mats.append(g)
+        pa = np.nonzero(perm == a)[0][0]
+        pb = np.nonzero(perm == b)[0][0]
+        perm[pa], perm[pb] = b, a
+    v_pairs, v_mats = [], []
+    for k in range(rzz_per_half - 1, -1, -1):
+        theta, dress = u_parts[k]
+        delta = float(rng.normal(0.0, angle_noise)) if angle_noise > 0 else 0.0
+        v_pairs.append(relabel_gate(u_pairs[k], perm))
+        v_mats.append(dress.conj().T @ rzz(-theta + delta))
+    planted = rng.integers(0, 2, size=n).astype(np.uint8)
+    oq, om = _oneq_layer(planted)
+    pairs = np.array(u_pairs + p_pairs + v_pairs, dtype=np.int32)
+    mats = np.array(u_mats + p_mats + v_mats)
+    return Circuit(n, pairs, mats, len(pairs) // 2, oq, om, planted, perm,
+                   {"family": "hqap_like_mirror", "rzz_per_half": rzz_per_half, "n_swaps": n_swaps,
+                    "angle_noise": angle_noise, "seed": seed})
+
+
 def random_circuit(n: int, n_gates: int, seed: int = 0, line: bool = False) -> Circuit:
     """A circuit with no mirror structure (Haar gates on random pairs), for checks where
     the MPO must reproduce an arbitrary unitary."""

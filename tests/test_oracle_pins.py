@@ -434,3 +434,43 @@ def test_unswapped_layouts_reproduce_the_permutation(parallel):
         out = int(np.argmax(np.abs(psi)))
         assert abs(abs(psi[out]) - 1.0) < 1e-12
         assert out == 1 << site_to_out[r.layout_r.pos[q]]
+
+
+# --- the HQAP-like workload (RZZ gates, one-qubit layers, swap insertions) ----------------
+
+def test_swap_as_native_gates_is_a_swap():
+    rng = np.random.default_rng(11)
+    g = W.swap_as_native_gates(rng)
+    assert len(g) == 3
+    assert np.max(np.abs(g[2] @ g[1] @ g[0] - W.SWAP4)) < 1e-14
+    for x in g:
+        assert np.max(np.abs(x.conj().T @ x - np.eye(4))) < 1e-14
+        assert np.max(np.abs(x - W.SWAP4)) > 1e-3
+
+
+def test_rzz_is_exp_of_zz():
+    theta = 0.7
+    zz = np.diag([1.0, -1.0, -1.0, 1.0])
+    assert np.max(np.abs(W.rzz(theta) - np.diag(np.exp(-0.5j * theta * np.diag(zz))))) < 1e-15
+
+
+def test_hqap_like_mirror_peaks_on_planted():
+    """Without angle noise C|0> = |s>; with it the planted string keeps most of the weight,
+    near the first-order estimate exp(-g sigma^2 / 4) (a sanity band)."""
+    c = W.hqap_like_mirror(10, 40, 3, 0.0, seed=2)
+    assert c.split_index == c.n_gates // 2 and c.n_gates == 2 * 40 + 9
+    psi = sv.run_circuit(c)
+    assert abs(abs(psi[to_index(c.planted)]) ** 2 - 1.0) < 1e-12
+    c = W.hqap_like_mirror(10, 40, 3, 0.1, seed=2)
+    p = np.abs(sv.run_circuit(c)) ** 2
+    assert np.argmax(p) == to_index(c.planted)
+    assert 0.75 < p.max() < 1.0
+
+
+def test_oracle_contracts_hqap_like_exactly():
+    """The oracle on an HQAP-like circuit with the cutoff inactive reproduces every amplitude of
+    the statevector (n = 8)."""
+    c = W.hqap_like_mirror(8, 24, 2, 0.1, seed=4)
+    r = mpo.contract(c, mpo.Config(eps=1e-14, chi_max=1 << 20, tau=200))
+    amps = mpo.amplitudes(mpo.project_zero(r), all_bits(8))
+    assert np.max(np.abs(amps - sv.run_circuit(c))) < 1e-11
