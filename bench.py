@@ -12,10 +12,15 @@ factorisations.  One bench step is one pass of the whole hot path in that regime
   factorise, truncate, split, size check), then one unswap stage (parallel variant, six
   parity batches), rewiring by layout;
   then project onto |0...0>, extract the peak (exact best-first search) and draw 1000 samples.
-value = (absorption updates + unswap trials) per second, every one a full two-site
-factorisation, summed over ranks (replicas: each rank runs its own seeded instance).
+value = two-site updates evaluated per second: absorption updates (each a full factorisation)
+plus unswap trials (each decided either by the library's lower-bound certificate or by a full
+factorisation), summed over ranks (replicas: each rank runs its own seeded instance); the
+line also gives the full updates and the trials apart, the batches of independent chi = 256
+updates of the microbenchmark (M0: 1, 8, 32 per launch, FP64 and mixed merges), the
+algorithmic-work roofline of the whole step, and the measured FP64 / FP32 peaks it uses.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --profile-case --chi 256 --batch 4 [--precision 0|1]   (one M0 launch)
 """
 from __future__ import annotations
 
@@ -40,8 +45,7 @@ UNIT = "updates/s"
 N_QUBITS, CHI_MAX, EPS, TAU = 28, 256, 1e-10, 1e6
 CURSOR = 12
 N_SAMPLES = 1000
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-JACOBI64_DRAM_BYTES = 1.50e9 + 66.38e9             # ncu: one FP64 Jacobi launch, four chi=256 updates
+M0_BATCHES = (1, 8, 32)
 
 
 def workload_name():
@@ -173,6 +177,88 @@ def oracle_sample(seed: int, budget_s: float, min_updates: int = 2):
     return done[0], t_end[0] - t0
 
 
+def oracle_sample_threads(seed: int, budget_s: float, threads: int):
+    """oracle_sample in a child process whose BLAS uses `threads` threads (the thread count is
+    fixed by the environment before numpy loads).  Returns (updates, seconds)."""
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"u, dt = bench.oracle_sample({seed}, {budget_s}); print(u, dt)")
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = str(threads)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=budget_s * 20 + 600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle child failed: {r.stderr[-2000:]}")
+    u, dt = r.stdout.strip().split()[-2:]
+    return int(u), float(dt)
+
+
+def m0_inputs(batch: int, chi: int, seed: int = 0):
+    """The microbenchmark's operands: `batch` independent two-site updates on disjoint bonds of
+    an MPO whose interior bonds are all at chi, with random right-isometric site tensors (QR of
+    complex Gaussians), geometric spectra exp(-k/64) and Haar 16 x 16 operators."""
+    n = 2 * batch + 10
+    chis = W.saturated_bond_dims(n, chi)
+    rng = W.rng_for(21, 1000 * seed + batch)
+    B = [W.random_right_isometry(rng, chis[j], chis[j + 1]) for j in range(n)]
+    lam = [W.geometric_spectrum(chis[b + 1], 64.0) for b in range(n - 1)]
+    ops = np.array([W.haar_unitary(rng, 16) for _ in range(batch)])
+    bonds = [4 + 2 * k for k in range(batch)]
+    return n, B, lam, ops, bonds
+
+
+def measure_m0(binding, batch: int, precision: int, chi: int = CHI_MAX, reps: int = 3, trials: bool = False,
+               device: int = 0):
+    """Batches of independent chi x chi updates through pc_apply_updates (one combined launch
+    set per batch), CUDA events on the library's stream, L2 flushed before each repetition.
+    With trials: one unswap stage on the same state (every trial has chi_old = chi_max)."""
+    import torch
+    n, B, lam, ops, bonds = m0_inputs(batch, chi)
+    ctx = binding.Context(eps=EPS, chi_max=chi, tau=1e12, precision=precision, device=device)
+    c = ctx.load_gates(n, np.zeros((0, 2), np.int32), np.zeros((0, 4, 4), complex))
+    stream = torch.cuda.ExternalStream(c.stream_handle())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    c.reset_timers(True)
+    for rep in range(reps + 1):
+        c.set_state(B, lam)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.apply_updates(bonds, ops)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+    st = c.stats()
+    out = {"batch": batch, "precision": ["fp64", "tf32x3 merges"][precision], "chi": chi,
+           "ms_per_launch_set": statistics.median(times), "updates_per_s": batch / (statistics.median(times) / 1e3),
+           "fp64_sweeps_max": st["max_sweeps"], "fp32_sweeps_max": st["max_sweeps_fp32"],
+           "deflated": st["n_deflated"], "fallbacks": st["fallbacks"]}
+    if trials:
+        c.set_state(B, lam)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        before = c.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.unswap()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st2 = c.stats()
+        nt = st2["n_trials"] - before["n_trials"]
+        out["trials"] = {"trials": nt, "certified": st2["n_trials_certified"] - before["n_trials_certified"],
+                         "ms": e0.elapsed_time(e1), "trials_per_s": nt / (e0.elapsed_time(e1) / 1e3),
+                         "note": "one parallel unswap stage on the same state: SWAP trials on every bond, "
+                                 "interior bond matrices 1024 x 1024 (ends smaller)"}
+    c.close()
+    ctx.close()
+    return out
+
+
 MIX_KW = dict(eps=1e-10, chi_max=64, tau=3000)
 MIX_COUNT = 8
 
@@ -277,6 +363,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2604_21908_gb300 import binding
 
+    fp64_peak, fp32_peak = binding.measure_alu_peaks(local)
     seed = rank
     circ = W.workload_unswap28(seed)
     extra = {"precondition_sweeps": args.pre_sweeps} if args.pre_sweeps > 0 else {}
@@ -304,7 +391,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     c.reset_timers(True)
-    units = 0
+    units = full = trials = certified = 0
+    alg_flops = 0.0
     dev_ms = 0.0
     stats = None
     for _ in range(args.steps):
@@ -318,6 +406,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         dev_ms += ev0.elapsed_time(ev1)
         units += stats["n_updates"] + stats["n_trials"]
+        full += stats["n_full"]
+        trials += stats["n_trials"]
+        certified += stats["n_trials_certified"]
+        alg_flops += stats["alg_flops"]
     launches, kms, kflops = c.timers()
     clk = clocks.stop()
     c.reset_timers(False)
@@ -342,45 +434,68 @@ def run_ours(args):
     c2.close()
 
     if rank == 0:
-        jac_launch = int(launches[1])
-        jac_ms = kms[1] / max(jac_launch, 1)
-        jac_flops = kflops[1] / max(jac_launch, 1)
-        achieved = jac_flops / (jac_ms * 1e-3) / 1e12 if jac_ms > 0 else 0.0
+        names = ["merge_gate", "factorisation", "truncate", "split", "other", "trial_certificate"]
+        share = {name: {"launches": int(launches[k]), "ms": float(kms[k]), "tflops": float(kflops[k] / 1e12)}
+                 for k, name in enumerate(names)}
+        timed = {k: kms[k] for k in (0, 1, 2, 3, 5)}
+        dom = max(timed, key=timed.get)
+        dom_launch = int(launches[dom])
+        dom_ms = kms[dom] / max(dom_launch, 1)
+        dom_flops = kflops[dom] / max(dom_launch, 1)
+        achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+        step_ms = t_max / args.steps
+        t_roof_ms = alg_flops / args.steps / (fp64_peak * 1e12) * 1e3
         cpu = None
         if world == 1:
-            u, dt = oracle_sample(seed, 20.0)
+            u, dt = oracle_sample_threads(seed, 20.0, cpu_cores())
+            u1, dt1 = oracle_sample_threads(seed, 20.0, 1)
             cpu = {"value": u / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"{u} two-site updates (the first of the step's layer pair, chi=256 interior) "
-                             f"on the saturated 28-qubit state, {dt:.1f} s"}
+                             f"on the saturated 28-qubit state, {dt:.1f} s, BLAS threads = cores",
+                   "one_thread": {"value": u1 / dt1, "cores": 1, "sample": f"{u1} updates, {dt1:.1f} s"}}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64c", "data": "synthetic",
             "config": {"workload": workload_name(), "n_qubits": N_QUBITS, "chi_max": CHI_MAX, "eps": EPS,
-                       "tau": TAU, "samples": N_SAMPLES, "updates_per_step": units // max(args.steps, 1),
+                       "tau": TAU, "samples": N_SAMPLES, "units_per_step": units // max(args.steps, 1),
                        "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write); "
                        "working set > L2"},
-            "time_to_peak_ms_per_step": t_max / args.steps,
+            "units": {"absorption_updates_per_step": stats["n_updates"], "unswap_trials_per_step": stats["n_trials"],
+                      "trials_certified_per_step": stats["n_trials_certified"],
+                      "full_factorisations_per_step": stats["n_full"], "deflated_per_step": stats["n_deflated"],
+                      "full_updates_per_s": full / (t_max / 1e3), "trials_per_s": trials / (t_max / 1e3)},
             "jacobi_sweeps": {"fp64_max": stats["max_sweeps"], "fp32_max": stats["max_sweeps_fp32"],
                               "fallbacks": stats["fallbacks"]},
-            "peak_probability": p,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": JACOBI64_DRAM_BYTES,
-                         "kernel": "bond factorisation phase of a wave: blocked FP32 preconditioning sweeps, "
-                                   "FP64 polar GEMMs and the FP64 jacobi_kernel (the dominant kernel)",
-                         "flops_per_launch": jac_flops, "ms_per_launch": jac_ms,
-                         "traffic_note": "dram read+write of one FP64 jacobi_kernel launch on four chi=256 "
-                                         "updates (ncu, profiles/jacobi_kernel_dram_chi256_batch4.md); the "
-                                         "bench's waves average 4.7 such updates",
-                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 pipe)"},
-            "kernel_share": {name: {"launches": int(launches[k]), "ms": float(kms[k]), "tflops": float(kflops[k] / 1e12)}
-                             for k, name in enumerate(["merge_gate", "jacobi", "truncate", "split", "other"])},
+            "peak_probability_of_step": p,
+            "measured_peaks": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak,
+                               "how": "FMA-chain kernel over every SM inside this run (pc_measure_alu_peaks), "
+                                      "best of three after a warm-up, CUDA events"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": None,
+                         "kernel": f"class '{names[dom]}' (the largest timed share of the step)",
+                         "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+                         "peak_source": "of measured: FP64 FMA-chain peak of this device in this run",
+                         "traffic_note": "null: the kernels changed since the last DRAM capture",
+                         "step": {"what": "whole step against the FP64 pipe: T_roof = algorithmic flops / "
+                                          "FP64 peak (updates 4(4L^2v+22v^3), trials values-only "
+                                          "4(4Lv^2-4v^3/3), merges and gates), frac = T_roof / T_measured; "
+                                          "the bytes term (16.8 MB per chi=256 update) is < 1e-4 of T_roof",
+                                  "alg_flops_per_step": alg_flops / args.steps, "t_roof_ms": t_roof_ms,
+                                  "t_measured_ms": step_ms, "frac": t_roof_ms / step_ms}},
+            "kernel_share": share,
             "gpu_launches": int(sum(launches)),
             "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sites_bytes + gate_bytes),
                     "d2h_bytes_per_step": int(N_SAMPLES * N_QUBITS + N_QUBITS + 8)},
             "cpu_baseline": cpu,
             "clocks": clk,
         }
+        if world == 1 and not args.no_m0:
+            m0 = [measure_m0(binding, b, 0, trials=(b == 8), device=local) for b in M0_BATCHES]
+            m0.append(measure_m0(binding, 8, 1, device=local))
+            line["m0"] = {"workload": "independent chi=256 updates (1024 x 1024 bond matrices), random right "
+                                      "isometries, geometric spectra exp(-k/64), Haar 16x16 operators, eps=1e-10, "
+                                      "chi_max=256", "runs": m0}
         if world == 1 and not args.no_serving:
             line["batching"] = measure_batching(binding)
             cap = MIX_COUNT / line["batching"]["batched_s"]        # circuits/s the batch sustains
@@ -396,6 +511,16 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One M0 configuration for a profiler: `--batch` independent chi=`--chi` updates,
+    `--repeat` times, printed as JSON (kernel classes, sweeps, updates/s)."""
+    import torch
+    from paper_2604_21908_gb300 import binding
+    torch.cuda.set_device(0)
+    out = measure_m0(binding, args.batch, args.precision, chi=args.chi, reps=args.repeat, trials=args.trials)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,8 +529,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-serving", action="store_true", help="skip the batching and serving measurements")
     ap.add_argument("--pre-sweeps", type=int, default=0, help="FP32 preconditioning sweep cap (0: library default)")
+    ap.add_argument("--no-m0", action="store_true", help="skip the batches of independent updates")
+    ap.add_argument("--profile-case", action="store_true", help="run one M0 configuration and exit")
+    ap.add_argument("--chi", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--trials", action="store_true", help="profile case: also one unswap stage")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -86,6 +86,21 @@ typedef struct pc_config {
   int32_t precondition_sweeps; /* cap on FP32 preconditioning sweeps (>= 1); the FP64 sweeps */
                              /* that follow run to convergence whatever this cap           */
   int32_t side_mode;         /* PC_SIDE_ALTERNATE or PC_SIDE_ADAPTIVE                      */
+  int32_t certify_trials;    /* 1: an unswap trial is first decided without its full      */
+                             /* factorisation when a rigorous lower bound shows that its   */
+                             /* count reaches the rejection threshold (the k-th singular   */
+                             /* value of a randomised FP64 projection, Sec. II.B.2 needs   */
+                             /* only the count); 0: every trial is a full factorisation.   */
+  int32_t deflate;           /* 1: when the chi_max cap decides the count, the FP64 sweeps */
+                             /* orthogonalise only what the kept vectors need (a floor set */
+                             /* from the FP32 sweeps, verified afterwards); 0: off         */
+  double fp32_dead_rel;      /* FP32 sweep floor (rows below sqrt(fp32_dead_rel) |X|_F are */
+                             /* left to the FP64 sweeps); 0: 1e-12 / rows                  */
+  int32_t recanonicalise;    /* 1 (default): after each absorption step, compress M to     */
+                             /* canonical form (Algorithm 1): a left-to-right QR sweep and */
+                             /* a right-to-left SVD sweep with the cutoff, restoring the   */
+                             /* Vidal/Hastings form that truncating updates drift from     */
+  int32_t pad_;
 } pc_config;
 
 /* Counters filled by pc_contract. */
@@ -103,6 +118,17 @@ typedef struct pc_stats {
                              /* the FP32 preconditioning                                  */
   double seconds;            /* host wall time of the call                                */
   int32_t max_sweeps_fp32;   /* largest FP32 preconditioning sweep count of one update     */
+  int32_t pad_;
+  int64_t n_trials_certified; /* unswap trials rejected by the lower-bound certificate     */
+  int64_t n_deflated;        /* factorisations finished with the deflation floor          */
+  int64_t n_full;            /* full factorisations (absorption updates and trials that   */
+                             /* ran the whole SVD)                                        */
+  int64_t n_recanon;         /* recanonicalisation sweeps (Algorithm 1 compression)        */
+  double alg_flops;          /* algorithmic work of the call's two-site updates: per       */
+                             /* absorption update 4(4 L^2 v + 22 v^3) (thin SVD with both  */
+                             /* vector sets, complex, L >= v the bond matrix sides), per   */
+                             /* unswap trial the values-only 4(4 L v^2 - 4 v^3 / 3), plus   */
+                             /* 8 m chi_m n + 2048 chi_l chi_r for every merge and gate     */
 } pc_stats;
 
 /* Fills cfg with the paper's defaults except eps/chi_max (1e-10 / 256) and tau (1e6). */
@@ -237,14 +263,22 @@ pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n
 
 /* Kernel accounting since the last pc_reset_kernel_timers.  Per kernel class (0 merge and
  * gate, 1 Jacobi factorisation, 2 truncation, 3 split, 4 everything else: environments,
- * peak search, sampling, one-qubit gates, accumulator set-up) the number of kernel launches
- * and, when timing is enabled, the total milliseconds measured with CUDA events on the
- * circuit's stream (class 4 is counted, not timed) and the algorithmic floating-point work:
+ * peak search, sampling, one-qubit gates, accumulator set-up, 5 unswap-trial certificates:
+ * projection, FP64 sweeps and norms) the number of kernel launches and, when timing is
+ * enabled, the total milliseconds measured with CUDA events on the circuit's stream (class 4
+ * is counted, not timed) and the floating-point work:
  * class 0: 8 * 4chi_l * chi_m * 4chi_r + 8 * 256 * chi_l * chi_r (complex merge + gate);
  * class 1: 4 * (4 M^2 N + 22 N^3) with M >= N the bond matrix sides (textbook thin SVD
- * with both singular-vector sets, complex); class 3: 8 * m * n * k (B_j = T0 V).
- * launches, ms, flops: arrays of length 5 (any may be NULL). */
+ * with both singular-vector sets, complex, per full factorisation); class 3: 8 * m * n * k
+ * (B_j = T0 V); class 5: the projection (8 r v L) and the rotations performed.
+ * launches, ms, flops: arrays of length 6 (any may be NULL). */
 pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops);
+
+/* Measured arithmetic peaks of the device (the denominators of the library's FP64 and FP32
+ * rooflines): an FMA-chain kernel over every SM (8 blocks of 256 threads per SM, 8
+ * independent chains per thread), best of three timed launches after a warm-up, CUDA
+ * events.  Writes TFLOP/s (2 flops per FMA) to the two host doubles.  Not in the paper. */
+pc_status pc_measure_alu_peaks(int32_t device, double* fp64_tflops, double* fp32_tflops);
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
 
 /* One bond factorisation that allocates no device memory.  The paper has no counterpart:

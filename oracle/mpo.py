@@ -48,6 +48,8 @@ class Config:
     unswap_parallel: bool = True    # App. A.1 parallel swap selection
     unswap_enabled: bool = True     # False = the plain Middle-MPO attack (Sec. I)
     side_adaptive: bool = False     # App. A.3 adaptive side selection (else alternate L, R)
+    recanonicalise: bool = True     # Algorithm 1 "compress M to canonical form" after each
+                                    # absorption step and before the projection
 
 
 def two_site_operator(g: np.ndarray | None = None, h: np.ndarray | None = None) -> np.ndarray:
@@ -153,6 +155,31 @@ class MPOState:
         t = self.trial(j, u16, cfg)
         self.commit(j, t)
         return t.count
+
+    def recanonicalise(self, cfg: Config) -> None:
+        """Algorithm 1, "compress M to canonical form via SVD with eps": a left-to-right QR
+        sweep leaves every site left-orthonormal and carries the rest to the right; a
+        right-to-left SVD sweep then makes every site right-canonical (B_j = V^dagger), reads
+        the bond's Schmidt values with everything to its left orthonormal, applies the cutoff
+        (s_k > eps s_0, at least 1, at most chi_max) and carries U S to the left.  Afterwards
+        the stored B_j and lam_j are the Vidal/Hastings form of the current operator (under
+        truncation the two-site updates drift away from it).  |M>> is renormalised."""
+        n = self.n
+        B = [b.copy() for b in self.B]
+        for j in range(n - 1):
+            cl, _, cr = B[j].shape
+            q, r = np.linalg.qr(B[j].reshape(cl * 4, cr))
+            B[j] = q.reshape(cl, 4, q.shape[1])
+            B[j + 1] = np.einsum("ab,bpc->apc", r, B[j + 1])
+        for j in range(n - 1, 0, -1):
+            cl, _, cr = B[j].shape
+            u, s, vh = scipy.linalg.svd(B[j].reshape(cl, 4 * cr), full_matrices=False, lapack_driver="gesvd")
+            k = truncation_count(s, cfg.eps, cfg.chi_max)
+            B[j] = np.ascontiguousarray(vh[:k].reshape(k, 4, cr))
+            self.lam[j - 1] = s[:k] / np.linalg.norm(s[:k])
+            B[j - 1] = np.einsum("apb,bc->apc", B[j - 1], u[:, :k] * s[None, :k])
+        B[0] = B[0] / np.linalg.norm(B[0])
+        self.B = B
 
     def apply_one_site(self, j: int, g2: np.ndarray, side: int) -> None:
         """A one-qubit gate on the out-legs (side left) or in-legs (side right) of site j;
@@ -411,6 +438,8 @@ class Contraction:
                 else:
                     self._absorb_left_layer()
                     self._absorb_right_layer()
+                if cfg.recanonicalise:
+                    st.recanonicalise(cfg)
                 first = False
             self.res.trace.append({"phase": "absorb", "stage": self.stage, "size": st.size(),
                                    "max_chi": max(st.bond_dims()) if self.n > 1 else 1,
@@ -452,7 +481,8 @@ class OutputMPS:
 def project_zero(res: Result) -> OutputMPS:
     """Algorithm 1 final step: apply M to |0...0> (in-legs set to 0, p = 2*o + 0), then the
     right environments env[j] = sum_sigma A_j^sigma env[j+1] A_j^sigma^dagger that give
-    every prefix marginal."""
+    every prefix marginal.  (With recanonicalisation the last absorption step already left M
+    in canonical form.)"""
     st = res.state
     n = st.n
     A = [np.ascontiguousarray(st.B[j][:, 0::2, :]) for j in range(n)]

@@ -27,14 +27,18 @@ class PcConfig(C.Structure):
     _fields_ = [("eps", C.c_double), ("chi_max", C.c_int32), ("tau", C.c_double),
                 ("max_unswap_iter", C.c_int32), ("accept_equal", C.c_int32), ("unswap_mode", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("device", C.c_int32), ("fp32_precondition", C.c_int32),
-                ("precision", C.c_int32), ("precondition_sweeps", C.c_int32), ("side_mode", C.c_int32)]
+                ("precision", C.c_int32), ("precondition_sweeps", C.c_int32), ("side_mode", C.c_int32),
+                ("certify_trials", C.c_int32), ("deflate", C.c_int32), ("fp32_dead_rel", C.c_double),
+                ("recanonicalise", C.c_int32), ("pad_", C.c_int32)]
 
 
 class PcStats(C.Structure):
     _fields_ = [("n_updates", C.c_int64), ("n_trials", C.c_int64), ("n_accepted", C.c_int64),
                 ("n_stages", C.c_int64), ("n_waves", C.c_int64), ("final_size", C.c_int64),
                 ("max_chi", C.c_int32), ("stalled", C.c_int32), ("max_sweeps", C.c_int32), ("fallbacks", C.c_int32),
-                ("seconds", C.c_double), ("max_sweeps_fp32", C.c_int32)]
+                ("seconds", C.c_double), ("max_sweeps_fp32", C.c_int32), ("pad_", C.c_int32),
+                ("n_trials_certified", C.c_int64), ("n_deflated", C.c_int64), ("n_full", C.c_int64),
+                ("n_recanon", C.c_int64), ("alg_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
@@ -94,7 +98,7 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_get_stats", "pc_get_trace", "pc_checkpoint_write", "pc_checkpoint_read", "pc_batch_create", "pc_batch_destroy",
            "pc_batch_attach", "pc_batch_detach", "pc_batch_contract", "pc_batch_counters", "pc_batch_set_timing",
            "pc_projected_bytes", "pc_server_create", "pc_server_submit", "pc_server_wait", "pc_server_get_stats",
-           "pc_server_clock", "pc_server_destroy"]
+           "pc_server_clock", "pc_server_destroy", "pc_measure_alu_peaks"]
 
 
 def _p(t):
@@ -155,6 +159,7 @@ def load(path: str = LIB_PATH):
         "pc_batch_counters": ([vp, _p(i64), _p(i64), _p(i32), vp, vp], i32),
         "pc_batch_set_timing": ([vp, i32], i32),
         "pc_projected_bytes": ([i32, i32, i64], i64),
+        "pc_measure_alu_peaks": ([i32, _p(dbl), _p(dbl)], i32),
         "pc_server_create": ([_p(PcServerConfig), _p(vp)], i32),
         "pc_server_submit": ([vp, _p(PcRequest), _p(i64)], i32),
         "pc_server_wait": ([vp, i64, dbl, _p(PcResult), vp, vp], i32),
@@ -181,6 +186,16 @@ def default_config(**kw) -> PcConfig:
     for k, v in kw.items():
         setattr(cfg, k, v)
     return cfg
+
+
+def measure_alu_peaks(device: int = 0) -> tuple[float, float]:
+    """pc_measure_alu_peaks: (FP64, FP32) FMA-chain TFLOP/s of the device."""
+    lib = load()
+    a, b = C.c_double(0), C.c_double(0)
+    st = lib.pc_measure_alu_peaks(device, C.byref(a), C.byref(b))
+    if st != PC_OK:
+        raise PcError(st, "pc_measure_alu_peaks")
+    return a.value, b.value
 
 
 def plan_routing(n_qubits: int, pairs: np.ndarray, split_index: int) -> np.ndarray:
@@ -412,10 +427,11 @@ class Circuit:
         self._chk(self.lib.pc_reset_kernel_timers(self.h, 1 if enable else 0), "pc_reset_kernel_timers")
 
     def timers(self):
-        """(launches, ms, flops) per kernel class: merge+gate, Jacobi, truncate, split, other."""
-        la = np.zeros(5, dtype=np.int64)
-        ms = np.zeros(5)
-        fl = np.zeros(5)
+        """(launches, ms, flops) per kernel class: merge+gate, factorisation, truncate, split,
+        other, unswap-trial certificates."""
+        la = np.zeros(6, dtype=np.int64)
+        ms = np.zeros(6)
+        fl = np.zeros(6)
         self._chk(self.lib.pc_kernel_timers(self.h, _ptr(la), _ptr(ms), _ptr(fl)), "pc_kernel_timers")
         return la, ms, fl
 
@@ -481,8 +497,8 @@ class Batch:
     def counters(self):
         la, ta = C.c_int64(0), C.c_int64(0)
         mt = C.c_int32(0)
-        ms = np.zeros(5)
-        fl = np.zeros(5)
+        ms = np.zeros(6)
+        fl = np.zeros(6)
         self.lib.pc_batch_counters(self.h, C.byref(la), C.byref(ta), C.byref(mt), _ptr(ms), _ptr(fl))
         return {"launches": la.value, "tasks": ta.value, "max_tasks": mt.value, "ms": ms, "flops": fl}
 

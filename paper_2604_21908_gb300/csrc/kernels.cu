@@ -2,9 +2,9 @@
 //
 // The hot path of every two-site update (Sec. II.B.1 of the paper: contract the gate with
 // the two MPO site tensors, then an SVD with cutoff eps) is split into
-//   merge      : X = B_j . B_j+1                         (batched complex FP64 GEMM)
-//   gate       : X <- U16 X on the 16-dim (p_j, p_j+1) index, T0 = copy without lambda,
-//                X scaled by lambda_{j-1} row-wise        (gate_apply_kernel)
+//   merge      : T0 = B_j . B_j+1                        (batched complex FP64 GEMM)
+//   gate       : T0 <- U16 T0 on the 16-dim (p_j, p_j+1) index; X = T0 scaled by
+//                lambda_{j-1} row-wise, transposed for a tall matrix (gate_apply_kernel)
 //   factorise  : one-sided Jacobi on the rows of X      (jacobi_kernel, cooperative)
 //   truncate   : sort row norms, relative cutoff, chi_max, renormalise (truncate_kernel)
 //   split      : B_j+1 = normalised kept rows (V^dagger), B_j = T0 V / |s| (GEMM)
@@ -122,8 +122,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
-// Gate application on the merged two-site tensor.  X[(l,p1), (p2,r)] holds
-// Theta[l, p1, p2, r]; for each (l, r) the 16-vector over P = 4 p1 + p2 is multiplied by U.
+// Gate application on the merged two-site tensor.  The merge leaves Theta[l, p1, p2, r] in T0 as
+// the (4 chi_l) x (4 chi_r) matrix T0[(l,p1), (p2,r)]; for each (l, r) the 16-vector over
+// P = 4 p1 + p2 is multiplied by U.  Each thread reads and rewrites its own 16 entries of T0
+// (the gated tensor without lambda) and writes the lambda-scaled entries to X, transposed for a
+// tall bond matrix: X is a different buffer, so the transposition never overwrites an entry
+// another thread has still to read.
 __global__ void __launch_bounds__(256) gate_apply_kernel(const UpdateTask* __restrict__ tasks) {
   const UpdateTask t = tasks[blockIdx.y];
   __shared__ double2 U[256];
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(256) gate_apply_kernel(const UpdateTask* __res
 #pragma unroll
   for (int p1 = 0; p1 < 4; ++p1)
 #pragma unroll
-    for (int p2 = 0; p2 < 4; ++p2) v[4 * p1 + p2] = t.X[(size_t)(4 * l + p1) * n + p2 * t.chi_r + r];
+    for (int p2 = 0; p2 < 4; ++p2) v[4 * p1 + p2] = t.T0[(size_t)(4 * l + p1) * n + p2 * t.chi_r + r];
   const double lam = t.lam_l ? t.lam_l[l] : 1.0;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -286,7 +290,9 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
   for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
     s_done[t] = 0;
     s_task[t] = tasks[t];
-    s_dead2[t] = s_task[t].fro2 ? (R)(s_task[t].dead_rel * *s_task[t].fro2) : R(0);
+    R d2 = s_task[t].fro2 ? (R)(s_task[t].dead_rel * *s_task[t].fro2) : R(0);
+    if (s_task[t].dead2_ovr) d2 = fmax(d2, (R)*s_task[t].dead2_ovr);
+    s_dead2[t] = d2;
     s_marg2[t] = R(6 * s_task[t].m) * s_dead2[t];
   }
   __syncthreads();
@@ -552,6 +558,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac_kernel(const typename JacT
     s_nbp[t] = nb + (nb & 1);
     s_done[t] = 0;
     s_dead2[t] = tk.fro2 ? (R)(tk.dead_rel * *tk.fro2) : R(0);
+    if (tk.dead2_ovr) s_dead2[t] = fmax(s_dead2[t], (R)*tk.dead2_ovr);
     s_marg2[t] = (R)(6 * tk.m) * s_dead2[t];
   }
   __syncthreads();
@@ -859,6 +866,7 @@ __device__ void truncate_body(const double2* X, int m, int n, double eps, int ch
     o.nrm = nrm;
     o.s_first_dropped = count < t.m ? sv[count] : 0.0;
     o.total2 = red[1];
+    o.s_last_kept = sv[count - 1];
     *out = o;
   }
 }
@@ -1008,6 +1016,103 @@ __global__ void amp_pick_kernel(const double2* W0, const double2* W1, const uint
   if (k >= K) return;
   const double2* W = site_bits[(size_t)k * n_sites + site] ? W1 : W0;
   for (int c = threadIdx.x; c < chi; c += blockDim.x) Vnext[(size_t)k * chi + c] = W[(size_t)k * chi + c];
+}
+
+// Recanonicalisation (Algorithm 1, "compress M to canonical form"): Z = X or X^T, X row-major
+// rows x cols.
+__global__ void recanon_load_kernel(const double2* __restrict__ X, int rows, int cols, int transpose,
+                                    double2* __restrict__ Z) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  Z[transpose ? (size_t)c * rows + r : (size_t)e] = X[e];
+}
+
+// One factor of a factorised Z (see recanon_emit in pc_internal.h).
+__global__ void recanon_emit_kernel(const double2* __restrict__ Z, const double2* __restrict__ Q, int ld,
+                                    const int32_t* __restrict__ idx, const double* __restrict__ sraw, int count,
+                                    int n_out, int use_q, int scale, int transpose_out, double2* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)count * n_out) return;
+  const int k = (int)(e / n_out), a = (int)(e % n_out);
+  const int row = idx[k];
+  double2 v;
+  if (use_q) {
+    const double2 q = Q[(size_t)row * ld + a];
+    v = make_double2(q.x, -q.y);
+  } else {
+    v = Z[(size_t)row * ld + a];
+  }
+  if (scale == 1) { const double inv = 1.0 / sraw[k]; v.x *= inv; v.y *= inv; }
+  else if (scale == 2) { const double s = sraw[k]; v.x *= s; v.y *= s; }
+  out[transpose_out ? (size_t)a * count + k : (size_t)k * n_out + a] = v;
+}
+
+// Deflation floor (see DeflateTask): one CTA per task.
+__global__ void __launch_bounds__(1024) deflate_floor_kernel(const DeflateTask* __restrict__ tasks) {
+  extern __shared__ unsigned char smem_raw[];
+  double* sv = reinterpret_cast<double*>(smem_raw);
+  const DeflateTask t = tasks[blockIdx.x];
+  int P = 1;
+  while (P < t.m) P <<= 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < P; i += nw) {
+    double acc = 0.0;
+    if (i < t.m) {
+      const float2* row = t.X32 + (size_t)i * t.n;
+      for (int k = lane; k < t.n; k += 32) {
+        const double x = row[k].x, y = row[k].y;
+        acc = fma(x, x, fma(y, y, acc));
+      }
+      acc = warp_sum(acc);
+    }
+    if (lane == 0) sv[i] = i < t.m ? sqrt(acc) : -1.0;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const double a = sv[i], b = sv[ixj];
+          const bool up = (i & k) == 0;
+          if (up ? (a < b) : (a > b)) { sv[i] = b; sv[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    double d2 = 0.0, sc = 0.0;
+    const double fro = sqrt(*t.fro2);
+    if (t.m > t.chi_max && t.chi_max >= 1) {
+      const double c = sv[t.chi_max - 1];
+      if (c >= 1e-4 * fro) {
+        sc = c;
+        const double d = c / (8.0 * t.m);
+        d2 = d * d;
+      }
+    }
+    *t.dead2_out = d2;
+    *t.sc_out = sc;
+  }
+}
+
+// FMA-chain throughput probe: every thread runs 8 independent chains of `iters` fused
+// multiply-adds (2 flops each); the result is written so the work cannot be removed.
+template <typename R>
+__global__ void __launch_bounds__(256) fma_probe_kernel(R a, R b, int iters, R* out) {
+  R x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (R)(threadIdx.x + k) * (R)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  R acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc += x[k];
+  if (acc == (R)12345.678) out[0] = acc;
 }
 
 __global__ void fill_ones_kernel(double2* v, int rows) {
@@ -1191,6 +1296,36 @@ cudaError_t launch_split_rows(const SplitRowsDesc* d_desc, int ntasks, int max_c
   return cudaGetLastError();
 }
 
+cudaError_t launch_deflate_floor(const DeflateTask* d_tasks, int ntasks, cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = TR_MAX * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(deflate_floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  deflate_floor_kernel<<<ntasks, 1024, smem, stream>>>(d_tasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recanon_load(const double2* X, int rows, int cols, int transpose, double2* Z, cudaStream_t stream) {
+  const long long cells = (long long)rows * cols;
+  if (cells <= 0) return cudaSuccess;
+  recanon_load_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, stream>>>(X, rows, cols, transpose, Z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recanon_emit(const double2* Z, const double2* Q, int ld, const int32_t* idx, const double* sraw,
+                                int count, int n_out, int use_q, int scale, int transpose_out, double2* out,
+                                cudaStream_t stream) {
+  const long long cells = (long long)count * n_out;
+  if (cells <= 0) return cudaSuccess;
+  recanon_emit_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, stream>>>(Z, Q, ld, idx, sraw, count, n_out, use_q,
+                                                                           scale, transpose_out, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_one_site(double2* B, int chi_l, int chi_r, const double2* g2_dev, int side,
                             cudaStream_t stream) {
   const long long cells = (long long)chi_l * 2 * chi_r;
@@ -1220,6 +1355,14 @@ cudaError_t launch_sample_pick(const double2* W0, const double2* W1, const doubl
 cudaError_t launch_amp_pick(const double2* W0, const double2* W1, const uint8_t* site_bits, int K, int chi,
                             int site, int n_sites, double2* Vnext, cudaStream_t stream) {
   amp_pick_kernel<<<K, 128, 0, stream>>>(W0, W1, site_bits, K, chi, site, n_sites, Vnext);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* out, cudaStream_t stream) {
+  if (fp64)
+    fma_probe_kernel<double><<<blocks, 256, 0, stream>>>(0.999999, 1e-9, iters, (double*)out);
+  else
+    fma_probe_kernel<float><<<blocks, 256, 0, stream>>>(0.999999f, 1e-9f, iters, (float*)out);
   return cudaGetLastError();
 }
 

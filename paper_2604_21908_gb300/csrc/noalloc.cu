@@ -62,6 +62,7 @@ __global__ void noalloc_setup_kernel(NoAllocScratch* s, int m, int n, int transp
   t.nrm2 = s->nrm2;
   t.fro2 = nullptr;
   t.stamp = s->stamp;
+  t.dead2_ovr = nullptr;
   for (int k = 0; k < NA_MAX_DIM; ++k) s->stamp[k] = -1;
   t.dead_rel = 0.0;
   t.m = transposed ? n : m;

@@ -22,6 +22,7 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <queue>
 #include <string>
@@ -195,12 +196,24 @@ struct Workspace {
   pc::GemmDesc *h_gemm2 = nullptr, *d_gemm2 = nullptr;
   unsigned int* d_bar = nullptr;
   int *d_err = nullptr, *h_err = nullptr;                // [0] Jacobi barrier, [1] tensor-core merge
-  // kernel accounting: 0 merge+gate, 1 factorisation, 2 truncation, 3 split, 4 other
+  // unswap-trial certificate: C = P X^H, its FP64 Jacobi and sorted row norms
+  pc::GemmDesc *h_cg = nullptr, *d_cg = nullptr;
+  pc::JacobiTask *h_jc = nullptr, *d_jc = nullptr;
+  pc::TruncTask *h_tc = nullptr, *d_tc = nullptr;
+  pc::TruncOut *h_ctout = nullptr, *d_ctout = nullptr;
+  pc::JacobiStatus *h_jst3 = nullptr, *d_jst3 = nullptr;
+  double *h_cfro2 = nullptr, *d_cfro2 = nullptr;
+  std::map<std::pair<int, int>, double2*> srft;          // (row length, rows) -> P on the device
+  // deflation floors of the FP64 sweeps
+  pc::DeflateTask *h_df = nullptr, *d_df = nullptr;
+  double *h_dead2 = nullptr, *d_dead2 = nullptr;         // [2][cap]: floor, s_c
+  // kernel accounting: 0 merge+gate, 1 factorisation, 2 truncation, 3 split, 4 other,
+  // 5 unswap-trial certificates
   bool timing = false;
   cudaEvent_t ev[6] = {};
-  int64_t t_launch[5] = {};
-  double t_ms[5] = {};
-  double t_flops[5] = {};
+  int64_t t_launch[6] = {};
+  double t_ms[6] = {};
+  double t_flops[6] = {};
   int64_t n_launches = 0;          // combined launches (batch accounting)
   int64_t n_tasks = 0;
   int max_tasks_seen = 0;
@@ -212,6 +225,11 @@ void ws_destroy(Workspace* w) {
   cudaFree(w->d_jt); cudaFree(w->d_jsub); cudaFree(w->d_jy); cudaFree(w->d_jfb); cudaFree(w->d_j32);
   cudaFree(w->d_q64); cudaFree(w->d_ns); cudaFree(w->d_tt); cudaFree(w->d_tout); cudaFree(w->d_jst);
   cudaFree(w->d_fro2); cudaFree(w->d_split); cudaFree(w->d_gemm2); cudaFree(w->d_bar); cudaFree(w->d_err);
+  cudaFree(w->d_cg); cudaFree(w->d_jc); cudaFree(w->d_tc); cudaFree(w->d_ctout); cudaFree(w->d_jst3);
+  cudaFree(w->d_cfro2); cudaFree(w->d_df); cudaFree(w->d_dead2);
+  cudaFreeHost(w->h_cg); cudaFreeHost(w->h_jc); cudaFreeHost(w->h_tc); cudaFreeHost(w->h_ctout);
+  cudaFreeHost(w->h_jst3); cudaFreeHost(w->h_cfro2); cudaFreeHost(w->h_df); cudaFreeHost(w->h_dead2);
+  for (auto& kv : w->srft) cudaFree(kv.second);
   cudaFreeHost(w->h_ops); cudaFreeHost(w->h_tasks); cudaFreeHost(w->h_merge); cudaFreeHost(w->h_jt);
   cudaFreeHost(w->h_jsub); cudaFreeHost(w->h_jy); cudaFreeHost(w->h_jfb); cudaFreeHost(w->h_j32);
   cudaFreeHost(w->h_q64); cudaFreeHost(w->h_ns); cudaFreeHost(w->h_tt); cudaFreeHost(w->h_tout);
@@ -258,6 +276,14 @@ cudaError_t ws_create(int cap, size_t arena_limit, int sm_count, cudaStream_t st
   dev(&w->d_gemm2, C); pin(&w->h_gemm2, C);
   dev(&w->d_bar, 2);
   dev(&w->d_err, 2); pin(&w->h_err, 2);
+  dev(&w->d_cg, C); pin(&w->h_cg, C);
+  dev(&w->d_jc, C); pin(&w->h_jc, C);
+  dev(&w->d_tc, C); pin(&w->h_tc, C);
+  dev(&w->d_ctout, C); pin(&w->h_ctout, C);
+  dev(&w->d_jst3, C); pin(&w->h_jst3, C);
+  dev(&w->d_cfro2, C); pin(&w->h_cfro2, C);
+  dev(&w->d_df, C); pin(&w->h_df, C);
+  dev(&w->d_dead2, 2 * C); pin(&w->h_dead2, 2 * C);
   for (auto& ev : w->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
   if (e != cudaSuccess) { ws_destroy(w); return e; }
@@ -304,6 +330,19 @@ struct pc_circuit {
   double* d_lam = nullptr;        // bond b spectrum at d_lam + b * chi_max
   double2* d_g2 = nullptr;
   pc::GemmDesc* h_gemm = nullptr; // [2] the circuit's own GEMMs (projection, sampling)
+  // recanonicalisation scratch (allocated on first use, sized by chi_max)
+  char* d_rc = nullptr;
+  struct {
+    double2 *Z, *Q, *T, *C;
+    double *nrm2, *lam, *sraw, *fro2;
+    int32_t *stamp, *idx;
+    pc::JacobiTask* jt;
+    pc::TruncTask* tt;
+    pc::TruncOut* tout;
+    pc::JacobiStatus* jst;
+    unsigned int* bar;
+    int* err;
+  } rc{};
   pc::GemmDesc* d_gemm = nullptr;
   Workspace* ws = nullptr;        // private workspace, created by the first standalone wave
   pc_batch* batch = nullptr;      // set while the circuit's waves go through a batch launcher
@@ -395,6 +434,7 @@ void free_circuit(pc_circuit* c) {
   ws_destroy(c->ws);
   cudaFree(c->d_sites); cudaFree(c->d_lam); cudaFree(c->d_g2); cudaFree(c->d_gemm); cudaFreeHost(c->h_gemm);
   cudaFree(c->d_env);
+  cudaFree(c->d_rc);
   cudaFree(c->d_snap_sites);
   cudaFree(c->d_snap_lam);
   for (auto& sv : c->saved) { cudaFree(sv.sites); cudaFree(sv.lam); }
@@ -478,6 +518,10 @@ struct WaveReq {
   const std::vector<int>* commit_mask = nullptr;
   bool decide_by_accept = false;
   bool accept_equal = false;
+  // unswap trials whose count only matters against the bond's current dimension (strict:
+  // count < chi_old accepts; equal: count <= chi_old): a certified lower bound that reaches
+  // the rejection threshold decides them without the full factorisation
+  bool trial_only = false;
   std::vector<int> counts, accepted;
   pc_status status = PC_OK;
   bool done = false;
@@ -509,12 +553,315 @@ pc_status chunk_fail(std::vector<FlatTask>& flat, size_t b0, size_t b1, pc_statu
                         std::string(#expr) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
+// Merge and gate of one launch: for each input, X = lambda-scaled gated merge (or its transpose
+// for a tall bond matrix) and T0 = the same without lambda (Sec. II.B.1: contract the gate with
+// the two site tensors).  FP64 merges run on gemm_kernel, mixed-precision ones on the tensor
+// cores.  Fills the workspace's operator, task and merge tables and launches on w->stream.
+struct MergeIn {
+  pc_circuit* c;
+  const WaveItem* it;
+  double2* X;
+  double2* T0;
+};
+
+cudaError_t stage_merge_gate(Workspace* w, const std::vector<MergeIn>& in) {
+  const int T = (int)in.size();
+  cudaStream_t s = w->stream;
+  std::vector<pc::GemmDesc> g64, gtc;
+  int max_cl = 0, max_cr = 0, tc_m = 0, tc_n = 0, tc_k = 0;
+  for (int t = 0; t < T; ++t) {
+    pc_circuit* c = in[t].c;
+    const int j = in[t].it->bond;
+    const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
+    const int m = 4 * cl, n = 4 * cr;
+    std::memcpy(w->h_ops + (size_t)t * 256, in[t].it->op, 256 * sizeof(cplx));
+    pc::UpdateTask& u = w->h_tasks[t];
+    u.Bl = site_ptr(c, j);
+    u.Br = site_ptr(c, j + 1);
+    u.lam_l = j > 0 ? lam_ptr(c, j - 1) : nullptr;
+    u.op = w->d_ops + (size_t)t * 256;
+    u.X = in[t].X;
+    u.T0 = in[t].T0;
+    u.chi_l = cl; u.chi_m = cm; u.chi_r = cr;
+    u.m = m; u.n = n;
+    u.transposed = m > n ? 1 : 0;
+    pc::GemmDesc g{};
+    g.A = u.Bl; g.B = u.Br; g.C = u.T0;   // the gate reads the merge from T0 and writes X
+    g.M = m; g.N = n; g.K = cm;
+    g.lda = cm; g.ldb = n; g.ldc = n;
+    g.opB = 0; g.alpha = 1.0; g.beta = 0.0;
+    if (c->ctx->cfg.precision == PC_PRECISION_TF32X3) {
+      gtc.push_back(g);
+      tc_m = std::max(tc_m, m); tc_n = std::max(tc_n, n); tc_k = std::max(tc_k, cm);
+    } else {
+      g64.push_back(g);
+    }
+    max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
+    const double mg = 8.0 * m * (double)cm * n + 8.0 * 256.0 * cl * (double)cr;
+    w->t_flops[0] += mg;
+    c->stats.alg_flops += mg;
+  }
+  const int n64 = (int)g64.size(), ntc = (int)gtc.size();
+  for (int i = 0; i < n64; ++i) w->h_merge[i] = g64[i];
+  for (int i = 0; i < ntc; ++i) w->h_merge[n64 + i] = gtc[i];
+  cudaError_t e = cudaSuccess;
+  if (ntc > 0) {
+    const size_t tb = pc::tc_merge_workspace_bytes(ntc, tc_m, tc_n, tc_k);
+    if (tb > w->tcws_bytes) {
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      cudaFree(w->d_tcws);
+      w->d_tcws = nullptr;
+      w->tcws_bytes = 0;
+      e = cudaMalloc(&w->d_tcws, tb);
+      if (e != cudaSuccess) return e;
+      w->tcws_bytes = tb;
+    }
+  }
+  if ((e = cudaMemcpyAsync(w->d_ops, w->h_ops, (size_t)T * 256 * sizeof(cplx), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(w->d_tasks, w->h_tasks, T * sizeof(pc::UpdateTask), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(w->d_merge, w->h_merge, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w->d_err, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+  timer_mark(w, 0);
+  if (n64 > 0) {
+    int mm = 0, nn = 0;
+    for (auto& g : g64) { mm = std::max(mm, g.M); nn = std::max(nn, g.N); }
+    if ((e = pc::launch_gemm(w->d_merge, n64, mm, nn, s)) != cudaSuccess) return e;
+    w->t_launch[0] += 1;
+  }
+  if (ntc > 0) {
+    // merge as complex 3xTF32 on the tensor cores (two launches: operand split, MMA)
+    e = pc::launch_tc_merge(w->d_merge + n64, ntc, tc_m, tc_n, tc_k, w->d_tcws, w->tcws_bytes, w->d_err + 1, s);
+    if (e != cudaSuccess) return e;
+    w->t_launch[0] += 2;
+  }
+  if ((e = pc::launch_gate_apply(w->d_tasks, T, max_cl, max_cr, s)) != cudaSuccess) return e;
+  w->t_launch[0] += 1;
+  return cudaSuccess;
+}
+
+// A fixed random projection with orthonormal rows (a subsampled randomised Fourier transform:
+// Woolfe, Liberty, Rokhlin and Tygert 2008): P[s][k] = e^{i (phi_k - 2 pi f_s k / L)} / sqrt(L)
+// with distinct frequencies f_s and phases phi_k drawn from SplitMix64.  Built once per
+// (L, r) on the host and kept on the device.
+cudaError_t srft_matrix(Workspace* w, int L, int r, double2** out) {
+  auto key = std::make_pair(L, r);
+  auto it = w->srft.find(key);
+  if (it != w->srft.end()) { *out = it->second; return cudaSuccess; }
+  std::vector<int> freq(L);
+  for (int k = 0; k < L; ++k) freq[k] = k;
+  for (int k = L - 1; k > 0; --k) {          // Fisher-Yates with a counter-based stream
+    const int j = (int)(splitmix64(0x5EED0000u + (uint64_t)L, (uint64_t)k) % (uint64_t)(k + 1));
+    std::swap(freq[k], freq[j]);
+  }
+  std::vector<double2> h((size_t)r * L);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double inv = 1.0 / std::sqrt((double)L);
+  std::vector<double> phi(L);
+  for (int k = 0; k < L; ++k)
+    phi[k] = two_pi * (double)(splitmix64(0xFA5E0000u + (uint64_t)L, (uint64_t)k) >> 11) * (1.0 / 9007199254740992.0);
+  for (int q = 0; q < r; ++q)
+    for (int k = 0; k < L; ++k) {
+      const double a = phi[k] - two_pi * (double)(((int64_t)freq[q] * k) % L) / (double)L;
+      h[(size_t)q * L + k] = make_double2(std::cos(a) * inv, std::sin(a) * inv);
+    }
+  double2* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, h.size() * sizeof(double2));
+  if (e != cudaSuccess) return e;
+  // stream-ordered and complete before the host buffer goes: a pageable cudaMemcpy may return
+  // before its DMA lands, and the kernels that read P run on a non-blocking stream
+  e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, w->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+  if (e != cudaSuccess) { cudaFree(d); return e; }
+  w->srft[key] = d;
+  *out = d;
+  return cudaSuccess;
+}
+
+// Rejection threshold of an unswap trial (App. A.1/A.2 and Algorithm 1): strict acceptance
+// rejects count >= chi_old, equal acceptance rejects count >= chi_old + 1.  0 when no count
+// the truncation can return reaches it (the trial must run in full).
+int trial_threshold(const FlatTask& f) {
+  if (!f.r->trial_only) return 0;
+  pc_circuit* c = f.r->c;
+  const int j = (*f.r->items)[f.k].bond;
+  const int v = std::min(4 * c->chi[j], 4 * c->chi[j + 2]);
+  const int k = c->chi[j + 1] + (f.r->accept_equal ? 1 : 0);
+  return k <= std::min(v, c->chi_max) ? k : 0;
+}
+
+constexpr int kCertOversample = 32;
+constexpr int kCertMinVectors = 128;
+
+// Scratch of one certificate: X and T0 of the trial (m x n each) and C = P X^H (r x v) with
+// its Jacobi and truncation vectors.
+size_t cert_bytes(int m, int n, int r) {
+  const size_t v = (size_t)std::min(m, n);
+  return 2 * al256((size_t)m * n * sizeof(double2)) + al256((size_t)r * v * sizeof(double2)) +
+         3 * al256((size_t)r * sizeof(double)) + 2 * al256((size_t)r * sizeof(int32_t));
+}
+
+int cert_rows(const FlatTask& f) {
+  const int k = trial_threshold(f);
+  if (k == 0) return 0;
+  pc_circuit* c = f.r->c;
+  const int j = (*f.r->items)[f.k].bond;
+  const int v = std::min(4 * c->chi[j], 4 * c->chi[j + 2]);
+  const int r = k + kCertOversample;
+  return (v >= kCertMinVectors && r <= v) ? r : 0;
+}
+
+// The certificate of a batch of unswap trials (Sec. II.B.2 needs only each trial's count).
+// For a trial with stored matrix Xs (v vectors of length L; its singular values are those of
+// the bond matrix) and threshold k: C = P Xs^H with the fixed projection P (r = k + 32
+// orthonormal rows), then the FP64 one-sided Jacobi on the r rows of C.  Interlacing gives
+// sigma_k(X) >= sigma_k(C) / |P|_2, and |P|_2 <= |P|_F.  With the k-th largest converged row
+// norm c_k of C, the rounding of the product (|dC|_F <= 4 gamma_L |P|_F |X|_F), the backward
+// error of the sweeps (<= 16 S r u |C|_F) and the residual orthogonality of the converged rows
+// (cosines <= tol, so sigma_k >= c_k sqrt(1 - k tol)), the trial is certified to keep at least
+// k values when
+//     c_k sqrt(1 - k tol) - 4 gamma_L |P|_F |X|_F - 16 S r u |C|_F  >  eps |X|_F |P|_F,
+// since s_0 <= |X|_F.  Certified trials are rejected without factorising the bond matrix;
+// the others are resolved[] = 0 and run the full factorisation afterwards.
+pc_status certify_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t b1,
+                        std::vector<char>& resolved) {
+  const int T = (int)(b1 - b0);
+  cudaStream_t s = w->stream;
+  size_t need = 0;
+  for (int t = 0; t < T; ++t) {
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const int j = (*f.r->items)[f.k].bond;
+    need += cert_bytes(4 * c->chi[j], 4 * c->chi[j + 2], cert_rows(f));
+  }
+  WS_TRY(ws_reserve(w, need));
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = w->d_arena + off;
+    off += al256(bytes);
+    return p;
+  };
+  std::vector<MergeIn> in(T);
+  std::vector<int> kk(T), rr(T), vv(T), ll(T);
+  int max_r = 0, max_v = 0, pairs = 0;
+  for (int t = 0; t < T; ++t) {
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const WaveItem& it = (*f.r->items)[f.k];
+    const int j = it.bond;
+    const int m = 4 * c->chi[j], n = 4 * c->chi[j + 2];
+    const int v = std::min(m, n), L = std::max(m, n);
+    const int r = cert_rows(f);
+    kk[t] = trial_threshold(f); rr[t] = r; vv[t] = v; ll[t] = L;
+    in[t] = {c, &it, (double2*)take((size_t)m * n * sizeof(double2)), (double2*)take((size_t)m * n * sizeof(double2))};
+    double2* Cm = (double2*)take((size_t)r * v * sizeof(double2));
+    double2* P = nullptr;
+    WS_TRY(srft_matrix(w, L, r, &P));
+    pc::GemmDesc& g = w->h_cg[t];
+    g = pc::GemmDesc{};
+    g.A = P; g.lda = L;
+    g.B = in[t].X; g.ldb = L; g.opB = 1;     // the stored matrix: v rows of length L
+    g.C = Cm; g.ldc = v;
+    g.M = r; g.N = v; g.K = L; g.alpha = 1.0;
+    pc::JacobiTask& jc = w->h_jc[t];
+    jc = pc::JacobiTask{};
+    jc.X = Cm;
+    jc.Q = nullptr;
+    jc.nrm2 = (double*)take((size_t)r * sizeof(double));
+    jc.fro2 = w->d_cfro2 + t;
+    jc.stamp = (int32_t*)take((size_t)r * sizeof(int32_t));
+    jc.dead2_ovr = nullptr;
+    const double dr = c->ctx->cfg.eps / (10.0 * r);
+    jc.dead_rel = dr * dr;
+    jc.m = r; jc.n = v; jc.mp = r + (r & 1);
+    pc::TruncTask& tt = w->h_tc[t];
+    tt = pc::TruncTask{};
+    tt.X = Cm;
+    tt.idx = (int32_t*)take((size_t)r * sizeof(int32_t));
+    tt.lam = (double*)take((size_t)r * sizeof(double));
+    tt.sraw = (double*)take((size_t)r * sizeof(double));
+    tt.out = w->d_ctout + t;
+    tt.eps = 0.0;
+    tt.m = r; tt.n = v;
+    tt.chi_max = kk[t];
+    // the bond matrix's own Jacobi task (for |X|_F^2)
+    pc::JacobiTask& jt = w->h_jt[t];
+    jt = pc::JacobiTask{};
+    jt.X = in[t].X; jt.m = v; jt.n = L; jt.mp = v + (v & 1);
+    max_r = std::max(max_r, r); max_v = std::max(max_v, v);
+    pairs += jc.mp / 2;
+  }
+  WS_TRY(stage_merge_gate(w, in));
+  timer_mark(w, 1);
+  WS_TRY(cudaMemcpyAsync(w->d_jt, w->h_jt, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_cg, w->h_cg, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_jc, w->h_jc, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_tc, w->h_tc, T * sizeof(pc::TruncTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(pc::launch_fro2(w->d_jt, T, w->d_fro2, s));
+  WS_TRY(pc::launch_gemm(w->d_cg, T, max_r, max_v, s));
+  WS_TRY(pc::launch_fro2(w->d_jc, T, w->d_cfro2, s));
+  WS_TRY(pc::launch_init_stamps(w->d_jc, T, max_r, s));
+  WS_TRY(cudaMemsetAsync(w->d_jst3, 0, T * sizeof(pc::JacobiStatus), s));
+  WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+  int max_sweeps = 1;
+  for (int t = 0; t < T; ++t) max_sweeps = std::max(max_sweeps, flat[b0 + t].r->c->ctx->cfg.jacobi_max_sweeps);
+  WS_TRY(pc::launch_jacobi(w->d_jc, T, w->d_jst3, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_v, pairs, s));
+  WS_TRY(pc::launch_truncate_tasks(w->d_tc, T, s));
+  timer_mark(w, 2);
+  w->t_launch[5] += 3;
+  w->t_launch[4] += 3;
+  WS_TRY(cudaMemcpyAsync(w->h_ctout, w->d_ctout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_jst3, w->d_jst3, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_fro2, w->d_fro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_cfro2, w->d_cfro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_err, w->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaStreamSynchronize(s));
+  if (w->timing) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, w->ev[0], w->ev[1]);
+    cudaEventElapsedTime(&b, w->ev[1], w->ev[2]);
+    w->t_ms[0] += a;
+    w->t_ms[5] += b;
+  }
+  for (int t = 0; t < T; ++t)   // the projection GEMM and the rotations of the FP64 sweeps
+    w->t_flops[5] += 8.0 * rr[t] * (double)vv[t] * ll[t] + 12.0 * w->h_jst3[t].sweeps * (double)rr[t] * rr[t] * vv[t];
+  if (w->h_err[0]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
+  if (w->h_err[1]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "a tensor-core merge wait exceeded its limit");
+  const double u = 1.1102230246251565e-16;
+  for (int t = 0; t < T; ++t) {
+    const FlatTask& f = flat[b0 + t];
+    const pc::TruncOut& o = w->h_ctout[t];
+    const pc::JacobiStatus& js = w->h_jst3[t];
+    const int k = kk[t], r = rr[t], L = ll[t], v = vv[t];
+    const double xf = std::sqrt(std::max(0.0, w->h_fro2[t])), cf = std::sqrt(std::max(0.0, w->h_cfro2[t]));
+    const double pf = std::sqrt((double)r) * (1.0 + 1e-12);
+    const double gam = L * u / (1.0 - L * u);
+    const double tol = 2.0 * u * std::sqrt((double)v);
+    const double dead = std::sqrt(w->h_jc[t].dead_rel) * cf, marg = std::sqrt(6.0 * r) * dead;
+    const double ck = o.s_last_kept;
+    const double lower = ck * std::sqrt(std::max(0.0, 1.0 - k * tol)) - 4.0 * gam * pf * xf -
+                         16.0 * js.sweeps * (double)r * u * cf;
+    const double eps = f.r->c->ctx->cfg.eps;
+    const bool ok = js.converged && o.count == k && ck > marg && lower > eps * xf * pf;
+    if (ok) {
+      resolved[b0 + t] = 1;
+      f.r->counts[f.k] = k;
+      f.r->accepted[f.k] = 0;
+      f.r->c->stats.n_trials_certified += 1;
+      f.r->c->stats.alg_flops += 4.0 * (4.0 * (double)L * v * v - 4.0 * (double)v * v * v / 3.0);
+    }
+  }
+  w->n_launches += 1;
+  w->n_tasks += T;
+  return PC_OK;
+}
+
 // Factorises and commits the tasks flat[b0, b1) in one set of launches on w->stream.
 pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t b1) {
   const int T = (int)(b1 - b0);
   cudaStream_t s = w->stream;
   std::vector<TaskScratch> sc(T);
-  std::vector<char> precond(T, 0), tc(T, 0);
+  std::vector<char> precond(T, 0);
   std::vector<int> m_of(T), n_of(T), v_of(T), bond_of(T);
   size_t need = 0;
   for (int t = 0; t < T; ++t) {
@@ -532,19 +879,17 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     off += al256(bytes);
     return p;
   };
-  int max_m = 0, max_n = 0, max_cl = 0, max_cr = 0, max_v = 0, max_len = 0, total_pairs = 0;
-  int tc_m = 0, tc_n = 0, tc_k = 0;
-  std::vector<pc::GemmDesc> g64, gtc;
+  int max_v = 0, max_len = 0, total_pairs = 0;
+  std::vector<MergeIn> min_(T);
   for (int t = 0; t < T; ++t) {
     const FlatTask& f = flat[b0 + t];
     pc_circuit* c = f.r->c;
     const WaveItem& it = (*f.r->items)[f.k];
     const int j = it.bond;
-    const int cl = c->chi[j], cm = c->chi[j + 1], cr = c->chi[j + 2];
+    const int cl = c->chi[j], cr = c->chi[j + 2];
     const int m = 4 * cl, n = 4 * cr, v = std::min(m, n), L = std::max(m, n);
     const bool transposed = m > n;
     m_of[t] = m; n_of[t] = n; v_of[t] = v; bond_of[t] = j;
-    tc[t] = c->ctx->cfg.precision == PC_PRECISION_TF32X3;
     TaskScratch& x = sc[t];
     x.X = (double2*)take((size_t)m * n * sizeof(double2));
     x.T0 = (double2*)take((size_t)m * n * sizeof(double2));
@@ -561,28 +906,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
       x.Qb = (double2*)take((size_t)v * v * sizeof(double2));
       x.Y = (double2*)take((size_t)m * n * sizeof(double2));
     }
-    std::memcpy(w->h_ops + (size_t)t * 256, it.op, 256 * sizeof(cplx));
-    pc::UpdateTask& u = w->h_tasks[t];
-    u.Bl = site_ptr(c, j);
-    u.Br = site_ptr(c, j + 1);
-    u.lam_l = j > 0 ? lam_ptr(c, j - 1) : nullptr;
-    u.op = w->d_ops + (size_t)t * 256;
-    u.X = x.X;
-    u.T0 = x.T0;
-    u.chi_l = cl; u.chi_m = cm; u.chi_r = cr;
-    u.m = m; u.n = n;
-    u.transposed = transposed ? 1 : 0;
-    pc::GemmDesc g{};
-    g.A = u.Bl; g.B = u.Br; g.C = u.X;
-    g.M = m; g.N = n; g.K = cm;
-    g.lda = cm; g.ldb = n; g.ldc = n;
-    g.opB = 0; g.alpha = 1.0; g.beta = 0.0;
-    if (tc[t]) {
-      gtc.push_back(g);
-      tc_m = std::max(tc_m, m); tc_n = std::max(tc_n, n); tc_k = std::max(tc_k, cm);
-    } else {
-      g64.push_back(g);
-    }
+    min_[t] = {c, &it, x.X, x.T0};
     // The Jacobi orthogonalises min(m, n) vectors: the rows of X, or for a tall bond matrix
     // its columns, with the rotations accumulated into Q (the right singular vectors).
     pc::JacobiTask& jt = w->h_jt[t];
@@ -591,6 +915,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     jt.nrm2 = x.nrm2;
     jt.fro2 = w->d_fro2 + t;
     jt.stamp = x.stamp;
+    jt.dead2_ovr = nullptr;
     jt.m = v;
     jt.n = L;
     jt.mp = v + (v & 1);
@@ -605,47 +930,17 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     tt.m = v; tt.n = L;
     tt.chi_max = c->chi_max;
     tt.pad_ = 0;
-    max_m = std::max(max_m, m); max_n = std::max(max_n, n); max_v = std::max(max_v, v);
+    max_v = std::max(max_v, v);
     max_len = std::max(max_len, L);
-    max_cl = std::max(max_cl, cl); max_cr = std::max(max_cr, cr);
     total_pairs += jt.mp / 2;
-    w->t_flops[0] += 8.0 * m * (double)cm * n + 8.0 * 256.0 * cl * (double)cr;
     w->t_flops[1] += 4.0 * (4.0 * (double)L * L * v + 22.0 * (double)v * v * v);
+    c->stats.n_full += 1;
+    c->stats.alg_flops += f.r->trial_only ? 4.0 * (4.0 * (double)L * v * v - 4.0 * (double)v * v * v / 3.0)
+                                          : 4.0 * (4.0 * (double)L * L * v + 22.0 * (double)v * v * v);
   }
-  const int n64 = (int)g64.size(), ntc = (int)gtc.size();
-  for (int i = 0; i < n64; ++i) w->h_merge[i] = g64[i];
-  for (int i = 0; i < ntc; ++i) w->h_merge[n64 + i] = gtc[i];
-  if (ntc > 0) {
-    const size_t tb = pc::tc_merge_workspace_bytes(ntc, tc_m, tc_n, tc_k);
-    if (tb > w->tcws_bytes) {
-      WS_TRY(cudaStreamSynchronize(s));
-      cudaFree(w->d_tcws);
-      w->d_tcws = nullptr;
-      w->tcws_bytes = 0;
-      WS_TRY(cudaMalloc(&w->d_tcws, tb));
-      w->tcws_bytes = tb;
-    }
-  }
-  WS_TRY(cudaMemcpyAsync(w->d_ops, w->h_ops, (size_t)T * 256 * sizeof(cplx), cudaMemcpyHostToDevice, s));
-  WS_TRY(cudaMemcpyAsync(w->d_tasks, w->h_tasks, T * sizeof(pc::UpdateTask), cudaMemcpyHostToDevice, s));
-  WS_TRY(cudaMemcpyAsync(w->d_merge, w->h_merge, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
+  WS_TRY(stage_merge_gate(w, min_));
   WS_TRY(cudaMemcpyAsync(w->d_jt, w->h_jt, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
   WS_TRY(cudaMemcpyAsync(w->d_tt, w->h_tt, T * sizeof(pc::TruncTask), cudaMemcpyHostToDevice, s));
-  WS_TRY(cudaMemsetAsync(w->d_err, 0, 2 * sizeof(int), s));
-  timer_mark(w, 0);
-  if (n64 > 0) {
-    int mm = 0, nn = 0;
-    for (auto& g : g64) { mm = std::max(mm, g.M); nn = std::max(nn, g.N); }
-    WS_TRY(pc::launch_gemm(w->d_merge, n64, mm, nn, s));
-    w->t_launch[0] += 1;
-  }
-  if (ntc > 0) {
-    // merge as complex 3xTF32 on the tensor cores (two launches: operand split, MMA)
-    WS_TRY(pc::launch_tc_merge(w->d_merge + n64, ntc, tc_m, tc_n, tc_k, w->d_tcws, w->tcws_bytes, w->d_err + 1, s));
-    w->t_launch[0] += 2;
-  }
-  WS_TRY(pc::launch_gate_apply(w->d_tasks, T, max_cl, max_cr, s));
-  w->t_launch[0] += 1;
   timer_mark(w, 1);
   WS_TRY(pc::launch_fro2(w->d_jt, T, w->d_fro2, s));
   WS_TRY(pc::launch_init_accumulators(w->d_jt, T, max_v, s));
@@ -676,7 +971,12 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     j32.nrm2 = reinterpret_cast<float*>(x.nrm2);
     j32.fro2 = jt.fro2;
     j32.stamp = x.stamp32;
-    j32.dead_rel = 1e-12 / jt.m;      // FP32 noise: a preconditioner may skip any pair
+    j32.dead2_ovr = nullptr;
+    {
+      // FP32 noise: a preconditioner may skip any pair below its floor
+      const double fr = flat[b0 + t].r->c->ctx->cfg.fp32_dead_rel;
+      j32.dead_rel = fr > 0.0 ? fr : 1e-12 / jt.m;
+    }
     j32.m = jt.m; j32.n = jt.n; j32.mp = jt.mp; j32.pad_ = 0;
     w->h_q64[i] = x.Q;
     const int v = jt.m, L = jt.n;
@@ -727,11 +1027,39 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
     WS_TRY(pc::launch_gemm(w->d_ns + 4 * P, P, pv, pl, s));
     w->t_launch[1] += 8;
   }
+  // Deflation floors of the FP64 sweeps (tasks with more vectors than chi_max, FP32 rows
+  // available): set on the device from the FP32 row norms, verified after the sweeps.
+  std::vector<char> defl(T, 0);
+  WS_TRY(cudaMemsetAsync(w->d_dead2, 0, 2 * (size_t)w->cap * sizeof(double), s));
+  {
+    int nd = 0;
+    for (int i = 0; i < P; ++i) {
+      const int t = psub[i];
+      pc_circuit* c = flat[b0 + t].r->c;
+      if (!c->ctx->cfg.deflate || v_of[t] <= c->chi_max) continue;
+      pc::DeflateTask& d = w->h_df[nd++];
+      d.X32 = sc[t].X32;
+      d.fro2 = w->d_fro2 + t;
+      d.dead2_out = w->d_dead2 + t;
+      d.sc_out = w->d_dead2 + w->cap + t;
+      d.m = v_of[t];
+      d.n = w->h_jt[t].n;
+      d.chi_max = c->chi_max;
+      d.pad_ = 0;
+      defl[t] = 1;
+    }
+    if (nd > 0) {
+      WS_TRY(cudaMemcpyAsync(w->d_df, w->h_df, nd * sizeof(pc::DeflateTask), cudaMemcpyHostToDevice, s));
+      WS_TRY(pc::launch_deflate_floor(w->d_df, nd, s));
+      w->t_launch[1] += 1;
+    }
+  }
   // FP64 sweeps: on Y = Q X for the preconditioned tasks (accumulating into Q on the column
   // path), on X itself for the others
   for (int t = 0; t < T; ++t) {
     w->h_jy[t] = w->h_jt[t];
     if (precond[t]) w->h_jy[t].X = sc[t].Y;
+    if (defl[t]) w->h_jy[t].dead2_ovr = w->d_dead2 + t;
   }
   WS_TRY(cudaMemcpyAsync(w->d_jy, w->h_jy, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
   WS_TRY(cudaMemsetAsync(w->d_jst, 0, T * sizeof(pc::JacobiStatus), s));
@@ -751,6 +1079,7 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
   WS_TRY(cudaMemcpyAsync(w->h_jst, w->d_jst, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
   WS_TRY(cudaMemcpyAsync(w->h_err, w->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   WS_TRY(cudaMemcpyAsync(w->h_fro2, w->d_fro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WS_TRY(cudaMemcpyAsync(w->h_dead2, w->d_dead2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (P > 0)
     WS_TRY(cudaMemcpyAsync(w->h_jst + w->cap, w->d_jst + w->cap, P * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
   WS_TRY(cudaStreamSynchronize(s));
@@ -774,7 +1103,17 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
   for (int t = 0; t < T; ++t) {
     if (!precond[t]) continue;
     const double x2 = w->h_fro2[t], y2 = w->h_tout[t].total2;
-    if (!(std::fabs(y2 - x2) <= 1e-9 * x2)) redo.push_back(t);
+    bool ok = std::fabs(y2 - x2) <= 1e-9 * x2;
+    // A deflated task is exact when it kept chi_max values and the smallest kept value lies
+    // above the Frobenius bound sqrt(6) m sqrt(dead2) of the block below the second floor.
+    const double d2 = w->h_dead2[t];
+    if (ok && d2 > 0.0) {
+      pc_circuit* c = flat[b0 + t].r->c;
+      const pc::TruncOut& o = w->h_tout[t];
+      ok = o.count == c->chi_max && o.s_last_kept > 1.01 * std::sqrt(6.0) * v_of[t] * std::sqrt(d2);
+      if (ok) c->stats.n_deflated += 1;
+    }
+    if (!ok) redo.push_back(t);
   }
   std::vector<double2*> final_x(T);
   for (int t = 0; t < T; ++t) final_x[t] = precond[t] ? sc[t].Y : sc[t].X;
@@ -893,15 +1232,46 @@ pc_status run_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t
 // Runs the waves of several circuits together (their items are pairwise disjoint within
 // each circuit; circuits share nothing), in chunks that fit the workspace.
 pc_status execute_waves(Workspace* w, std::vector<WaveReq*>& reqs) {
-  std::vector<FlatTask> flat;
+  std::vector<FlatTask> all;
   for (WaveReq* r : reqs) {
     r->status = PC_OK;
     r->counts.assign(r->items->size(), 0);
     r->accepted.assign(r->items->size(), 0);
-    for (int k = 0; k < (int)r->items->size(); ++k) flat.push_back({r, k});
+    for (int k = 0; k < (int)r->items->size(); ++k) all.push_back({r, k});
+  }
+  pc_status worst = PC_OK;
+  // unswap trials with a rejection threshold first go through the certificate
+  std::vector<FlatTask> cand;
+  for (const FlatTask& f : all)
+    if (f.r->c->ctx->cfg.certify_trials && cert_rows(f) > 0) cand.push_back(f);
+  std::vector<char> resolved(cand.size(), 0);
+  for (size_t pos = 0; pos < cand.size();) {
+    size_t end = pos, need = 0;
+    while (end < cand.size() && (int)(end - pos) < w->cap) {
+      const FlatTask& f = cand[end];
+      pc_circuit* c = f.r->c;
+      const int j = (*f.r->items)[f.k].bond;
+      const size_t b = cert_bytes(4 * c->chi[j], 4 * c->chi[j + 2], cert_rows(f));
+      if (need + b > w->arena_limit && end > pos) break;
+      need += b;
+      ++end;
+    }
+    pc_status st = certify_chunk(w, cand, pos, end, resolved);
+    if (st != PC_OK) worst = st;
+    pos = end;
+  }
+  std::vector<FlatTask> flat;
+  {
+    size_t ci = 0;
+    for (const FlatTask& f : all) {
+      if (ci < cand.size() && cand[ci].r == f.r && cand[ci].k == f.k) {
+        if (!resolved[ci++]) flat.push_back(f);
+      } else {
+        flat.push_back(f);
+      }
+    }
   }
   size_t pos = 0;
-  pc_status worst = PC_OK;
   while (pos < flat.size()) {
     size_t end = pos, need = 0;
     while (end < flat.size() && (int)(end - pos) < w->cap) {
@@ -979,7 +1349,7 @@ void batch_leave(pc_batch* b) {
 // One circuit's wave: through its batch launcher if attached, else on its own workspace.
 pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vector<int>& counts,
                    const std::vector<int>* commit_mask, bool decide_by_accept, bool accept_equal,
-                   std::vector<int>* accepted_out) {
+                   std::vector<int>* accepted_out, bool trial_only = false) {
   counts.assign(items.size(), 0);
   if (items.empty()) return PC_OK;
   if ((int)items.size() > c->max_tasks) return fail(c->ctx, PC_ERR_INVALID_ARG, "wave wider than the task limit");
@@ -989,6 +1359,7 @@ pc_status run_wave(pc_circuit* c, const std::vector<WaveItem>& items, std::vecto
   req.commit_mask = commit_mask;
   req.decide_by_accept = decide_by_accept;
   req.accept_equal = accept_equal;
+  req.trial_only = trial_only;
   pc_status st;
   if (c->batch) {
     pc_batch* b = c->batch;
@@ -1199,6 +1570,152 @@ pc_status absorb_step_adaptive(pc_circuit* c) {
   return st;
 }
 
+// One factorisation of a recanonicalisation step (Algorithm 1, "compress M to canonical form
+// via SVD"): Z = X (rows x cols) or its transpose, so that Z has no more rows than columns;
+// the FP64 one-sided Jacobi orthogonalises the rows of Z with the rotations W accumulated;
+// the row norms (singular values) are sorted and cut (s_k > eps s_0, at most chi_max).
+// Returns the kept count in *count (host).
+pc_status recanon_factor(pc_circuit* c, const double2* X, int rows, int cols, bool transpose, double eps,
+                         int chi_max, int* count) {
+  pc_ctx* ctx = c->ctx;
+  auto& r = c->rc;
+  const int mz = transpose ? cols : rows, nz = transpose ? rows : cols;
+  CUDA_TRY(ctx, pc::launch_recanon_load(X, rows, cols, transpose ? 1 : 0, r.Z, c->stream));
+  pc::JacobiTask jt{};
+  jt.X = r.Z; jt.Q = r.Q; jt.nrm2 = r.nrm2; jt.fro2 = r.fro2; jt.stamp = r.stamp; jt.dead2_ovr = nullptr;
+  const double dr = (eps > 0.0 ? eps : 1e-14) / (10.0 * mz);
+  jt.dead_rel = dr * dr;
+  jt.m = mz; jt.n = nz; jt.mp = mz + (mz & 1);
+  pc::TruncTask tt{};
+  tt.X = r.Z; tt.idx = r.idx; tt.lam = r.lam; tt.sraw = r.sraw; tt.out = r.tout;
+  tt.eps = eps; tt.m = mz; tt.n = nz; tt.chi_max = chi_max;
+  CUDA_TRY(ctx, cudaMemcpyAsync(r.jt, &jt, sizeof(jt), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(r.tt, &tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(r.jst, 0, sizeof(pc::JacobiStatus), c->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(r.bar, 0, 2 * sizeof(unsigned int), c->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(r.err, 0, sizeof(int), c->stream));
+  CUDA_TRY(ctx, pc::launch_fro2(r.jt, 1, r.fro2, c->stream));
+  CUDA_TRY(ctx, pc::launch_init_accumulators(r.jt, 1, mz, c->stream));
+  CUDA_TRY(ctx, pc::launch_init_stamps(r.jt, 1, mz, c->stream));
+  CUDA_TRY(ctx, pc::launch_jacobi(r.jt, 1, r.jst, ctx->cfg.jacobi_max_sweeps, r.bar, r.err, ctx->sm_count, nz,
+                                  jt.mp / 2, c->stream));
+  CUDA_TRY(ctx, pc::launch_truncate_tasks(r.tt, 1, c->stream));
+  count_launch(c, 6);
+  pc::TruncOut o;
+  pc::JacobiStatus js;
+  int err = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&o, r.tout, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(&js, r.jst, sizeof(js), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(&err, r.err, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+  if (err) return fail(ctx, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit (recanonicalisation)");
+  if (!js.converged) return fail(ctx, PC_ERR_NOCONVERGE, "one-sided Jacobi reached the sweep cap (recanonicalisation)");
+  if (!(o.s0 > 0.0)) return fail(ctx, PC_ERR_STATE, "a site tensor of the MPO vanished (recanonicalisation)");
+  *count = o.count;
+  return PC_OK;
+}
+
+// Algorithm 1, "compress M to canonical form via SVD with eps".  A left-to-right sweep makes
+// every site left-orthonormal (a QR step written as X = U (S V^dagger): U stays, S V^dagger
+// moves into the next site); a right-to-left sweep then factorises each site with everything
+// to its left orthonormal: B_j <- V^dagger (right-canonical), lambda_{j-1} <- the singular
+// values (the bond's Schmidt values, cut at eps s_0 and chi_max, renormalised), U S moves into
+// the previous site.  The result is the Vidal/Hastings form of the operator the sites hold;
+// |M>> is renormalised.  Only numerically zero values (below 1e-14 s_0) are dropped by the
+// first sweep.
+pc_status recanonicalise(pc_circuit* c) {
+  pc_ctx* ctx = c->ctx;
+  const int n = c->n, X = c->chi_max;
+  auto& r = c->rc;
+  if (!c->d_rc) {
+    const size_t cap2 = (size_t)X * X, big = 4 * cap2;
+    size_t off = 0;
+    auto sz = [&](size_t b) { const size_t o = off; off += al256(b); return o; };
+    const size_t oZ = sz(big * sizeof(double2)), oQ = sz(cap2 * sizeof(double2)), oT = sz(big * sizeof(double2)),
+                 oC = sz(cap2 * sizeof(double2)), oN = sz(X * sizeof(double)), oL = sz(X * sizeof(double)),
+                 oS = sz(X * sizeof(double)), oF = sz(sizeof(double)), oSt = sz(X * sizeof(int32_t)),
+                 oI = sz(X * sizeof(int32_t)), oJ = sz(sizeof(pc::JacobiTask)), oTt = sz(sizeof(pc::TruncTask)),
+                 oO = sz(sizeof(pc::TruncOut)), oJs = sz(sizeof(pc::JacobiStatus)), oB = sz(2 * sizeof(unsigned int)),
+                 oE = sz(sizeof(int));
+    CUDA_TRY(ctx, cudaMalloc(&c->d_rc, off));
+    char* b = c->d_rc;
+    r.Z = (double2*)(b + oZ); r.Q = (double2*)(b + oQ); r.T = (double2*)(b + oT); r.C = (double2*)(b + oC);
+    r.nrm2 = (double*)(b + oN); r.lam = (double*)(b + oL); r.sraw = (double*)(b + oS); r.fro2 = (double*)(b + oF);
+    r.stamp = (int32_t*)(b + oSt); r.idx = (int32_t*)(b + oI); r.jt = (pc::JacobiTask*)(b + oJ);
+    r.tt = (pc::TruncTask*)(b + oTt); r.tout = (pc::TruncOut*)(b + oO); r.jst = (pc::JacobiStatus*)(b + oJs);
+    r.bar = (unsigned int*)(b + oB); r.err = (int*)(b + oE);
+  }
+  auto gemm = [&](const double2* A, int lda, const double2* Bm, int ldb, double2* C, int ldc, int M, int N,
+                  int K) -> pc_status {
+    pc::GemmDesc g{};
+    g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb; g.C = C; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
+    g.opB = 0; g.alpha = 1.0; g.beta = 0.0;
+    c->h_gemm[0] = g;
+    CUDA_TRY(ctx, cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(ctx, pc::launch_gemm(c->d_gemm, 1, M, N, c->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+    count_launch(c);
+    return PC_OK;
+  };
+  // left-to-right: site j = U, R = S V^dagger into site j+1
+  for (int j = 0; j + 1 < n; ++j) {
+    const int cl = c->chi[j], cr = c->chi[j + 1], cn = c->chi[j + 2];
+    const bool tall = 4 * cl >= cr;
+    int k = 0;
+    pc_status st = recanon_factor(c, site_ptr(c, j), 4 * cl, cr, tall, 1e-14, 1 << 30, &k);
+    if (st != PC_OK) return st;
+    if (tall) {
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, nullptr, 4 * cl, r.idx, r.sraw, k, 4 * cl, 0, 1, 1, site_ptr(c, j), c->stream));
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, r.Q, cr, r.idx, r.sraw, k, cr, 1, 2, 0, r.C, c->stream));
+    } else {
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, r.Q, 4 * cl, r.idx, r.sraw, k, 4 * cl, 1, 0, 1, site_ptr(c, j), c->stream));
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, nullptr, cr, r.idx, r.sraw, k, cr, 0, 0, 0, r.C, c->stream));
+    }
+    count_launch(c, 2);
+    st = gemm(r.C, cr, site_ptr(c, j + 1), 4 * cn, r.T, 4 * cn, k, 4 * cn, cr);
+    if (st != PC_OK) return st;
+    CUDA_TRY(ctx, cudaMemcpyAsync(site_ptr(c, j + 1), r.T, (size_t)k * 4 * cn * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    c->chi[j + 1] = k;
+  }
+  // right-to-left: site j = V^dagger, lambda_{j-1} = S, U S into site j-1
+  for (int j = n - 1; j >= 1; --j) {
+    const int cl = c->chi[j], cr = c->chi[j + 1], cp = c->chi[j - 1];
+    const bool wide = cl <= 4 * cr;
+    int k = 0;
+    pc_status st = recanon_factor(c, site_ptr(c, j), cl, 4 * cr, !wide, ctx->cfg.eps, c->chi_max, &k);
+    if (st != PC_OK) return st;
+    if (wide) {
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, nullptr, 4 * cr, r.idx, r.sraw, k, 4 * cr, 0, 1, 0, site_ptr(c, j), c->stream));
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, r.Q, cl, r.idx, r.sraw, k, cl, 1, 2, 1, r.C, c->stream));
+    } else {
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, r.Q, 4 * cr, r.idx, r.sraw, k, 4 * cr, 1, 0, 0, site_ptr(c, j), c->stream));
+      CUDA_TRY(ctx, pc::launch_recanon_emit(r.Z, nullptr, cl, r.idx, r.sraw, k, cl, 0, 0, 1, r.C, c->stream));
+    }
+    count_launch(c, 2);
+    CUDA_TRY(ctx, cudaMemcpyAsync(lam_ptr(c, j - 1), r.lam, k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    st = gemm(site_ptr(c, j - 1), cl, r.C, k, r.T, k, 4 * cp, k, cl);
+    if (st != PC_OK) return st;
+    CUDA_TRY(ctx, cudaMemcpyAsync(site_ptr(c, j - 1), r.T, (size_t)4 * cp * k * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    c->chi[j] = k;
+  }
+  // renormalise |M>> (site 0 carries the norm)
+  const size_t n0 = (size_t)4 * c->chi[1];
+  std::vector<double2> h(n0);
+  CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), site_ptr(c, 0), n0 * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+  double nn = 0.0;
+  for (const double2& v : h) nn += v.x * v.x + v.y * v.y;
+  const double inv = 1.0 / std::sqrt(nn);
+  for (double2& v : h) { v.x *= inv; v.y *= inv; }
+  CUDA_TRY(ctx, cudaMemcpyAsync(site_ptr(c, 0), h.data(), n0 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
+  c->projected = false;
+  c->stats.n_recanon += 1;
+  return PC_OK;
+}
+
 pc_status absorb_layer_pair(pc_circuit* c) {
   std::vector<ResolvedOp> ops;
   bool do_oneq = false;
@@ -1246,7 +1763,7 @@ pc_status unswap_parallel(pc_circuit* c, int* n_acc) {
           items[k].bond = bonds[base + k];
           swap_op(side, items[k].op);
         }
-        pc_status st = run_wave(c, items, counts, nullptr, true, ctx->cfg.accept_equal != 0, &acc);
+        pc_status st = run_wave(c, items, counts, nullptr, true, ctx->cfg.accept_equal != 0, &acc, true);
         if (st != PC_OK) return st;
         c->stats.n_trials += (int64_t)cnt;
         for (size_t k = 0; k < cnt; ++k) {
@@ -1289,7 +1806,7 @@ pc_status unswap_sequential(pc_circuit* c, int* n_acc) {
     for (int side = 0; side < 3; ++side) {
       items[0].bond = i;
       swap_op(side, items[0].op);
-      pc_status st = run_wave(c, items, counts, &none, false, false, nullptr);
+      pc_status st = run_wave(c, items, counts, &none, false, ctx->cfg.accept_equal != 0, nullptr, true);
       if (st != PC_OK) return st;
       c->stats.n_trials += 1;
       if (counts[0] < best_cnt) { best_cnt = counts[0]; best_side = side; }
@@ -1401,6 +1918,10 @@ void pc_default_config(pc_config* cfg) {
   cfg->precision = PC_PRECISION_FP64;
   cfg->precondition_sweeps = 20;
   cfg->side_mode = PC_SIDE_ALTERNATE;
+  cfg->certify_trials = 1;
+  cfg->deflate = 1;
+  cfg->fp32_dead_rel = 0.0;
+  cfg->recanonicalise = 1;
 }
 
 pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
@@ -1409,7 +1930,8 @@ pc_status pc_create(const pc_config* cfg, pc_ctx** out) {
   if (!(cfg->eps >= 0.0) || cfg->chi_max < 1 || cfg->chi_max > 1024 || !(cfg->tau > 0.0) ||
       cfg->max_unswap_iter < 0 || cfg->jacobi_max_sweeps < 1 || cfg->unswap_mode < 0 || cfg->unswap_mode > 2 ||
       cfg->precision < PC_PRECISION_FP64 || cfg->precision > PC_PRECISION_TF32X3 || cfg->precondition_sweeps < 1 ||
-      cfg->side_mode < PC_SIDE_ALTERNATE || cfg->side_mode > PC_SIDE_ADAPTIVE)
+      cfg->side_mode < PC_SIDE_ALTERNATE || cfg->side_mode > PC_SIDE_ADAPTIVE || !(cfg->fp32_dead_rel >= 0.0) ||
+      cfg->fp32_dead_rel >= 1.0)
     return PC_ERR_INVALID_ARG;
   auto* ctx = new pc_ctx();
   ctx->cfg = *cfg;
@@ -1516,6 +2038,7 @@ pc_status pc_contract_iterations(pc_circuit* c, int32_t max_iterations, pc_stats
     bool first = true;
     while ((first || (double)mpo_size(c) < tau) && layers_remain(c)) {
       st = ctx->cfg.side_mode == PC_SIDE_ADAPTIVE ? absorb_step_adaptive(c) : absorb_layer_pair(c);
+      if (st == PC_OK && ctx->cfg.recanonicalise) st = recanonicalise(c);
       if (st != PC_OK) return st;
       first = false;
     }
@@ -1692,13 +2215,16 @@ pc_status pc_checkpoint_read(pc_circuit* c, const char* path) {
   size_t so = 0, lo = 0;
   for (int j = 0; j < n; ++j) {
     const size_t cnt = (size_t)chi[j] * 4 * chi[j + 1];
-    CUDA_TRY(ctx, cudaMemcpy(site_ptr(c, j), sites.data() + so, cnt * sizeof(double2), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpyAsync(site_ptr(c, j), sites.data() + so, cnt * sizeof(double2), cudaMemcpyHostToDevice,
+                                  c->stream));
     so += cnt;
   }
   for (int b = 0; b + 1 < n; ++b) {
-    CUDA_TRY(ctx, cudaMemcpy(lam_ptr(c, b), lam.data() + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpyAsync(lam_ptr(c, b), lam.data() + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
     lo += chi[b + 1];
   }
+  CUDA_TRY(ctx, cudaStreamSynchronize(c->stream));
   c->chi = chi;
   for (int side = 0; side < 2; ++side) {
     const std::vector<int>& pos = side == 0 ? pos0 : pos1;
@@ -1768,13 +2294,17 @@ pc_status pc_set_state(pc_circuit* c, const int32_t* chi, const double* sites, c
   size_t so = 0, lo = 0;
   for (int j = 0; j < c->n; ++j) {
     const size_t cnt = (size_t)chi[j] * 4 * chi[j + 1];
-    CUDA_TRY(c->ctx, cudaMemcpy(site_ptr(c, j), sites + 2 * so, cnt * sizeof(double2), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->ctx, cudaMemcpyAsync(site_ptr(c, j), sites + 2 * so, cnt * sizeof(double2), cudaMemcpyHostToDevice,
+                                     c->stream));
     so += cnt;
   }
   for (int b = 0; b + 1 < c->n; ++b) {
-    CUDA_TRY(c->ctx, cudaMemcpy(lam_ptr(c, b), lam + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->ctx, cudaMemcpyAsync(lam_ptr(c, b), lam + lo, chi[b + 1] * sizeof(double), cudaMemcpyHostToDevice,
+                                     c->stream));
     lo += chi[b + 1];
   }
+  // the uploads are complete before any launch on another stream reads the sites
+  CUDA_TRY(c->ctx, cudaStreamSynchronize(c->stream));
   for (int k = 0; k <= c->n; ++k) c->chi[k] = chi[k];
   c->lay[0].reset(c->n);
   c->lay[1].reset(c->n);
@@ -2020,7 +2550,12 @@ pc_status pc_sample(pc_circuit* c, int64_t n_samples, uint64_t seed, uint8_t* bi
     uint8_t* d_sb = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&d_u, u.size() * sizeof(double)));
     if (cudaMalloc(&d_sb, (size_t)rows * n) != cudaSuccess) { cudaFree(d_u); return fail(ctx, PC_ERR_OOM, "sample bits"); }
-    cudaMemcpy(d_u, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpyAsync(d_u, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaFree(d_u);
+      cudaFree(d_sb);
+      return fail(ctx, PC_ERR_CUDA, "uniforms upload");
+    }
     st = sweep_rows(c, rows, d_u, d_sb, true, nullptr);
     sb.resize((size_t)rows * n);
     if (st == PC_OK) cudaMemcpy(sb.data(), d_sb, sb.size(), cudaMemcpyDeviceToHost);
@@ -2052,7 +2587,12 @@ pc_status pc_amplitudes(pc_circuit* c, int64_t k, const uint8_t* bits, double* a
     double2* d_amp = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&d_sb, sb.size()));
     if (cudaMalloc(&d_amp, rows * sizeof(double2)) != cudaSuccess) { cudaFree(d_sb); return fail(ctx, PC_ERR_OOM, "amplitudes"); }
-    cudaMemcpy(d_sb, sb.data(), sb.size(), cudaMemcpyHostToDevice);
+    if (cudaMemcpyAsync(d_sb, sb.data(), sb.size(), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaFree(d_sb);
+      cudaFree(d_amp);
+      return fail(ctx, PC_ERR_CUDA, "bit strings upload");
+    }
     st = sweep_rows(c, rows, nullptr, d_sb, false, d_amp);
     res.resize(rows);
     if (st == PC_OK && cudaMemcpy(res.data(), d_amp, rows * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -2150,7 +2690,7 @@ pc_status pc_batch_counters(pc_batch* b, int64_t* launches, int64_t* tasks, int3
   if (launches) *launches = b->ws->n_launches;
   if (tasks) *tasks = b->ws->n_tasks;
   if (max_tasks) *max_tasks = b->ws->max_tasks_seen;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     if (ms) ms[k] = b->ws->t_ms[k];
     if (flops) flops[k] = b->ws->t_flops[k];
   }
@@ -2171,13 +2711,49 @@ int64_t pc_projected_bytes(int32_t n_qubits, int32_t chi_max, int64_t n_samples)
 
 pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double* flops) {
   if (check_circuit(c) != PC_OK) return PC_ERR_INVALID_ARG;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     const Workspace* w = c->ws;
     if (launches) launches[k] = (w ? w->t_launch[k] : 0) + (k == 4 ? c->other_launches : 0);
     if (ms) ms[k] = w ? w->t_ms[k] : 0.0;
     if (flops) flops[k] = w ? w->t_flops[k] : 0.0;
   }
   return PC_OK;
+}
+
+pc_status pc_measure_alu_peaks(int32_t device, double* fp64_tflops, double* fp32_tflops) {
+  if (!fp64_tflops || !fp32_tflops) return PC_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return PC_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PC_ERR_CUDA;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void* out = nullptr;
+  pc_status res = PC_OK;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess || cudaMalloc(&out, 16) != cudaSuccess)
+    res = PC_ERR_CUDA;
+  const int blocks = sms * 8;
+  for (int fp64 = 1; fp64 >= 0 && res == PC_OK; --fp64) {
+    const int iters = fp64 ? 4096 : 65536;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && res == PC_OK; ++rep) {   // first launch is a warm-up
+      float ms = 0.0f;
+      if (cudaEventRecord(e0, st) != cudaSuccess || pc::launch_fma_probe(fp64, blocks, iters, out, st) != cudaSuccess ||
+          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        res = PC_ERR_CUDA;
+        break;
+      }
+      const double flops = 2.0 * 8.0 * (double)iters * 256.0 * blocks;
+      if (rep > 0 && ms > 0.0f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    (fp64 ? *fp64_tflops : *fp32_tflops) = best;
+  }
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  return res;
 }
 
 pc_status pc_get_stream(pc_circuit* c, void** stream) {
@@ -2191,7 +2767,7 @@ pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable) {
   c->other_launches = 0;
   c->timing = enable != 0;
   if (c->ws) {
-    for (int k = 0; k < 5; ++k) { c->ws->t_launch[k] = 0; c->ws->t_ms[k] = 0.0; c->ws->t_flops[k] = 0.0; }
+    for (int k = 0; k < 6; ++k) { c->ws->t_launch[k] = 0; c->ws->t_ms[k] = 0.0; c->ws->t_flops[k] = 0.0; }
     c->ws->timing = c->timing;
   }
   return PC_OK;

@@ -36,7 +36,8 @@ struct UpdateTask {
   const double2* op;      // 16x16 operator on (p_j, p_j+1), row-major
   double2* X;             // Jacobi input: the merged, gated, lambda-scaled bond matrix,
                           // m x n row-major, or its transpose (n x m) when transposed
-  double2* T0;            // m x n: merged and gated, without lambda
+  double2* T0;            // m x n: the merge (written by the merge GEMM), then gated in
+                          // place by the gate kernel (without lambda)
   int32_t chi_l, chi_m, chi_r;
   int32_t m, n;           // 4*chi_l, 4*chi_r
   int32_t transposed;     // 1 when m > n: the Jacobi orthogonalises the n columns
@@ -56,12 +57,15 @@ struct UpdateTask {
 // stamp (m entries, set to -1 by the caller before the launch) records the round in which
 // each row was last rotated: a pair neither of whose rows changed since the pair's own
 // check one sweep earlier has the same inner product and is skipped.
+// dead2_ovr (nullable): a device value that raises dead2 above dead_rel * |X|_F^2 (the
+// deflation floor set after the FP32 sweeps when the chi_max cap decides the count).
 struct JacobiTask {
   double2* X;             // m x n row-major; rows are orthogonalised in place
   double2* Q;             // optional m x m accumulator (nullptr: none)
   double* nrm2;           // m squared row norms (scratch owned by the kernel)
   const double* fro2;     // squared Frobenius norm of X (or nullptr)
   int32_t* stamp;         // m rounds of last rotation (scratch, -1 at launch)
+  const double* dead2_ovr;
   double dead_rel;
   int32_t m, n;
   int32_t mp;             // m rounded up to even
@@ -74,6 +78,7 @@ struct JacobiTask32 {
   float* nrm2;
   const double* fro2;
   int32_t* stamp;
+  const double* dead2_ovr;
   double dead_rel;
   int32_t m, n;
   int32_t mp;
@@ -95,6 +100,7 @@ struct TruncOut {
   double nrm;             // sqrt(sum of kept s^2)
   double s_first_dropped; // first singular value not kept (0 if none)
   double total2;          // sum of the squares of all row norms (= squared Frobenius norm)
+  double s_last_kept;     // smallest kept singular value (unnormalised)
 };
 
 // Launch wrappers (all asynchronous on `stream`; return cudaError_t of the launch).
@@ -158,6 +164,32 @@ struct SplitRowsDesc {
 };
 cudaError_t launch_split_rows(const SplitRowsDesc* d_desc, int ntasks, int max_count, int max_n,
                               cudaStream_t stream);
+// Deflation floor of the FP64 sweeps from the FP32 preconditioned rows.  For each task: the
+// row norms of X32 (accumulated in FP64), sorted; s_c = the chi_max-th largest.  When the
+// matrix has more than chi_max rows and s_c >= 1e-4 |X|_F (far above the FP32 rounding
+// level), dead2_out = (s_c / (8 m))^2, else 0 (no deflation).  With that floor every row
+// above the second floor 6 m dead2 ends orthogonal to every row, and the rows below it form
+// a block of Frobenius norm <= sqrt(6) s_c / 8 < s_c: the chi_max largest singular values
+// and their vectors are exact (checked after the FP64 sweeps, see pc_api.cpp).
+struct DeflateTask {
+  const float2* X32;      // m x n, the FP32 rows after the preconditioning sweeps
+  const double* fro2;     // |X|_F^2 of the FP64 matrix
+  double* dead2_out;
+  double* sc_out;         // s_c (0 when not deflated)
+  int32_t m, n;
+  int32_t chi_max;
+  int32_t pad_;
+};
+cudaError_t launch_deflate_floor(const DeflateTask* d_tasks, int ntasks, cudaStream_t stream);
+// Recanonicalisation steps: Z = X (rows x cols, row-major) or its transpose.
+cudaError_t launch_recanon_load(const double2* X, int rows, int cols, int transpose, double2* Z, cudaStream_t stream);
+// After the one-sided Jacobi of Z (rows of length ld; rotations W in Q, ld x ld, when given) and
+// the sort of its row norms (idx, sraw: kept rows, descending), one factor: element (k, a) for
+// kept row k and a < n_out is conj(W[idx_k][a]) (use_q) or Z[idx_k][a], divided (scale 1) or
+// multiplied (scale 2) by sraw_k, written to out[k][a] or, transposed, out[a][k].
+cudaError_t launch_recanon_emit(const double2* Z, const double2* Q, int ld, const int32_t* idx, const double* sraw,
+                                int count, int n_out, int use_q, int scale, int transpose_out, double2* out,
+                                cudaStream_t stream);
 cudaError_t launch_one_site(double2* B, int chi_l, int chi_r, const double2* g2_dev, int side,
                             cudaStream_t stream);
 // Peak search: children of a prefix vector v (length chi_l) through site tensor B_j:
@@ -175,6 +207,8 @@ cudaError_t launch_sample_pick(const double2* W0, const double2* W1, const doubl
 cudaError_t launch_amp_pick(const double2* W0, const double2* W1, const uint8_t* site_bits, int K,
                             int chi, int site, int n_sites, double2* Vnext, cudaStream_t stream);
 cudaError_t launch_fill_ones(double2* v, int rows, cudaStream_t stream);
+// FMA-chain probe: blocks x 256 threads x 8 chains x iters FMAs in FP64 (fp64 = 1) or FP32.
+cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* out, cudaStream_t stream);
 
 // Mixed-precision merge on tcgen05 tensor cores (merge_tc.cu): for each descriptor of the
 // batch, C = A * B (opB = 0, alpha = 1, beta = 0, no row scaling) as complex 3xTF32 with FP32

@@ -41,6 +41,9 @@ def test_bench_configuration_first_gate_matches_oracle():
     c.set_state(B, lam)
     for j, u16 in ops:
         c.apply_updates([j], u16[None])
+    # the chi = 256 interior updates ran with the deflated FP64 sweeps (exactness is checked
+    # by the library after the sweeps; the comparisons below check the results)
+    assert c.stats()["n_deflated"] >= 1
 
     assert list(c.bond_dims()) == ctr.state.bond_dims()
     for bond in range(N - 1):
@@ -54,3 +57,37 @@ def test_bench_configuration_first_gate_matches_oracle():
     assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
     c.close()
     ctx.close()
+
+
+def test_unswap_stage_certificate_matches_full_trials_and_oracle():
+    """One parallel unswap stage (App. A.1) on the saturated 28-qubit state, its trials decided
+    by the lower-bound certificate and, separately, by full factorisations: identical unswap
+    logs, bond dimensions and spectra (1e-10).  The decisions of the first batch (SWAPs from
+    both sides on the even bonds) equal the oracle's full-SVD counts against chi_old."""
+    B, lam = W.peaked_saturated_state(N, CHI, 0)
+    res = {}
+    for certify in (1, 0):
+        ctx = binding.Context(eps=EPS, chi_max=CHI, tau=1e6, certify_trials=certify)
+        c = ctx.load_gates(N, np.zeros((0, 2), np.int32), np.zeros((0, 4, 4), complex))
+        c.set_state(B, lam)
+        c.unswap()
+        res[certify] = (list(c.unswap_log().tolist()), list(c.bond_dims()),
+                        [c.spectrum(b) for b in range(N - 1)], c.stats())
+        c.close()
+        ctx.close()
+    log1, dims1, spec1, st1 = res[1]
+    log0, dims0, spec0, st0 = res[0]
+    assert log1 == log0 and dims1 == dims0
+    for a, b in zip(spec1, spec0):
+        np.testing.assert_allclose(a, b, atol=1e-10, rtol=0)
+    assert st1["n_trials_certified"] > 0 and st0["n_trials_certified"] == 0
+    assert st1["n_trials"] == st0["n_trials"]
+
+    st = mpo.MPOState(N)
+    st.B = [b.copy() for b in B]
+    st.lam = [l.copy() for l in lam]
+    cfg = mpo.Config(eps=EPS, chi_max=CHI, tau=1e6)
+    op = mpo.swap_operator(mpo.SIDE_BOTH)
+    want = [b for b in range(0, N - 1, 2) if st.trial(b, op, cfg).count < st.chi(b)]
+    got = [rec[3] for rec in log1 if rec[1] == 0 and rec[2] == mpo.SIDE_BOTH and rec[3] % 2 == 0]
+    assert got == want

@@ -474,3 +474,42 @@ def test_oracle_contracts_hqap_like_exactly():
     r = mpo.contract(c, mpo.Config(eps=1e-14, chi_max=1 << 20, tau=200))
     amps = mpo.amplitudes(mpo.project_zero(r), all_bits(8))
     assert np.max(np.abs(amps - sv.run_circuit(c))) < 1e-11
+
+
+# --- recanonicalisation (Algorithm 1: compress M to canonical form) -----------------------
+
+def test_recanonicalise_restores_vidal_form_of_a_truncated_state():
+    """After truncating updates the stored lam drift from the Schmidt values of the operator
+    the sites hold; recanonicalisation (cutoff inactive) keeps that operator (up to the norm)
+    and makes every B right-canonical with lam = its operator-Schmidt values across each cut
+    (brute force on the dense 4^n tensor)."""
+    c = W.random_circuit(6, 16, seed=3)
+    r = mpo.contract(c, mpo.Config(eps=1e-3, chi_max=6, tau=1e12, recanonicalise=False))
+    st = r.state
+    t0 = dense_from_mpo(st)
+    t0 = t0 / np.linalg.norm(t0)
+    drift = max(np.max(np.abs(sv.operator_schmidt_values(t0, j)[:len(st.lam[j])] - st.lam[j])) for j in range(5))
+    assert drift > 1e-3                     # the truncated Hastings form has drifted
+    st.recanonicalise(mpo.Config(eps=1e-14, chi_max=1 << 20))
+    t1 = dense_from_mpo(st)
+    assert np.max(np.abs(t1 / np.linalg.norm(t1) - t0)) < 1e-12
+    for j in range(6):
+        m = st.B[j].reshape(st.B[j].shape[0], -1)
+        if j > 0:
+            assert np.max(np.abs(m @ m.conj().T - np.eye(m.shape[0]))) < 1e-12
+    for j in range(5):
+        s_ref = sv.operator_schmidt_values(t0, j)
+        k = len(st.lam[j])
+        assert np.max(np.abs(st.lam[j] - s_ref[:k])) < 1e-12
+        assert np.all(s_ref[k:] < 1e-12)
+
+
+def test_recanonicalise_is_the_identity_on_an_exact_vidal_state():
+    c = W.random_circuit(6, 14, seed=0)
+    r = mpo.contract(c, mpo.Config(eps=1e-14, chi_max=1 << 20, tau=1e12))
+    lam = [l.copy() for l in r.state.lam]
+    t0 = dense_from_mpo(r.state)
+    r.state.recanonicalise(mpo.Config(eps=1e-14, chi_max=1 << 20))
+    assert np.max(np.abs(dense_from_mpo(r.state) - t0)) < 1e-13
+    for a, b in zip(lam, r.state.lam):
+        assert np.max(np.abs(a - b)) < 1e-13
