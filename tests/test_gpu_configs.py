@@ -4,9 +4,10 @@
   path, 2048 x 1024 on the column path), FP64 and 3xTF32 merges;
 * the 28-qubit unswapping configuration's output: the exact peak, its probability and 1000
   samples of the saturated state, against the oracle's search and sampler on the same state;
-* the 28-qubit unswapping workload's generator at reduced size (12 qubits) end to end, and the
+* the 28-qubit unswapping workload's generator at reduced size end to end (10 qubits: solved;
+  12 qubits: where the method fails and only the discrete results are determined), and the
   HQAP-like workload (RZZ gates, one-qubit layers, swap insertions) at reduced size with the
-  paper's cutoff 2e-3 and adaptive sides (App. A.3, A.4), both against the oracle and the
+  paper's cutoff 2e-3 and adaptive sides (App. A.3, A.4), against the oracle and the
   statevector.
 Tolerances as in test_gpu_parity (FP64) and test_gpu_mixed (mixed precision)."""
 import numpy as np
@@ -69,20 +70,43 @@ def test_unswap28_saturated_peak_and_samples():
 
 
 def test_unswap28_generator_reduced_end_to_end():
-    """The 28-qubit unswapping workload's generator at 12 qubits (40 Haar gates per half, a
-    random hidden permutation of all 12 qubits, perturbation 0.02, chi_max = 64, eps = 1e-10):
+    """The 28-qubit unswapping workload's generator at 10 qubits (30 Haar gates per half, a random
+    hidden permutation of all 10 qubits, perturbation 0.02, chi_max = 64, eps = 1e-10, tau = 3000):
     plans, unswap logs, layouts, bond dimensions, spectra, peak, samples and trace equal the
-    oracle's.  At this cap neither finds the planted string although the statevector puts
-    most of the weight on it: the random permutation is not undone by adjacent swaps before
-    the truncated MPO loses it (the library reproduces the method, including where it fails)."""
-    circ = W.hidden_permutation_mirror(12, 40, 0.02, seed=0)
+    oracle's, and the peak is the planted string (the statevector's argmax)."""
+    circ = W.hidden_permutation_mirror(10, 30, 0.02, seed=0)
     ref, ctx, c, _ = run_both(circ, eps=1e-10, chi_max=64, tau=3000)
     bits, p = compare_runs(ref, c, circ)
-    psi = sv.run_circuit(circ)
-    probs = np.abs(psi) ** 2
+    assert np.array_equal(bits, circ.planted)
+    probs = np.abs(sv.run_circuit(circ)) ** 2
+    assert int(np.argmax(probs)) == sum(int(b) << q for q, b in enumerate(circ.planted))
+
+
+def test_unswap28_generator_where_the_method_fails():
+    """At 12 qubits (40 gates per half, chi_max = 64) the random hidden permutation is not undone
+    by adjacent swaps before the truncated MPO loses it: the statevector puts most of the weight
+    on the planted string, the method keeps a few per cent of it at best.  Every cut there is
+    truncated at the cap with near-degenerate singular values, so only the discrete results are
+    determined: the oracle itself, with LAPACK's divide-and-conquer SVD in place of gesvd, keeps
+    the same plan but moves the final spectra by 0.1 and changes the peak.  Compared: plans
+    (with the bond dimension after every update), unswap logs, layouts and bond dimensions; the
+    library's spectra are checked to be normalised and sorted, its peak probability small."""
+    circ = W.hidden_permutation_mirror(12, 40, 0.02, seed=0)
+    ref, ctx, c, _ = run_both(circ, eps=1e-10, chi_max=64, tau=3000)
+    plan_ref = np.array([[r.side, r.bond, r.kind, r.gate, r.chi] for r in ref.plan], np.int32).reshape(-1, 5)
+    assert np.array_equal(c.plan(), plan_ref)
+    assert np.array_equal(c.unswap_log(), np.array(ref.unswap_log, np.int32).reshape(-1, 4))
+    lay_l, lay_r = c.layouts()
+    assert list(lay_l) == ref.layout_l.pos and list(lay_r) == ref.layout_r.pos
+    assert list(c.bond_dims()) == ref.state.bond_dims()
+    for b in range(circ.n_qubits - 1):
+        s = c.spectrum(b)
+        assert abs(np.sum(s ** 2) - 1.0) < 1e-12 and np.all(np.diff(s) <= 1e-15)
+    bits, p, norm2 = c.extract_peak()
+    assert 0.0 < p < 0.5
+    probs = np.abs(sv.run_circuit(circ)) ** 2
     s_idx = sum(int(b) << q for q, b in enumerate(circ.planted))
     assert np.argmax(probs) == s_idx and probs[s_idx] > 0.9
-    assert not np.array_equal(bits, circ.planted)
 
 
 def test_hqap_like_reduced_end_to_end():
