@@ -279,6 +279,19 @@ pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double*
  * independent chains per thread), best of three timed launches after a warm-up, CUDA
  * events.  Writes TFLOP/s (2 flops per FMA) to the two host doubles.  Not in the paper. */
 pc_status pc_measure_alu_peaks(int32_t device, double* fp64_tflops, double* fp32_tflops);
+
+/* Autotuner of the FP64 one-sided Jacobi launch (the library's choice, not the paper's): for
+ * each shape i (lens[i] x lens[i] complex bond matrices, batches[i] of them in one launch;
+ * 4 <= lens <= 4096, 1 <= batches <= 64) it times two sweeps of seeded random matrices with 1,
+ * 2 and 4 warps per row pair (CUDA events, best of two after a warm-up), installs the fastest
+ * width in the process-wide table the launches consult (keyed by ceil(log2 row length) and
+ * floor(log2 row pairs per round)), and appends the table entries to the text file `path`
+ * (NULL: no file).  ms_out (may be NULL): double[n_shapes][3], milliseconds per width.  The
+ * widths change only the rounding order of the sweeps. */
+pc_status pc_autotune(int32_t device, int32_t n_shapes, const int32_t* lens, const int32_t* batches,
+                      const char* path, double* ms_out);
+/* Installs a table written by pc_autotune (lines "len_bucket pairs_bucket width ..."). */
+pc_status pc_load_tuning(const char* path);
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
 
 /* One bond factorisation that allocates no device memory.  The paper has no counterpart:

@@ -98,7 +98,7 @@ EXPORTS = ["pc_version", "pc_default_config", "pc_create", "pc_destroy", "pc_las
            "pc_restore", "pc_get_stream", "pc_factorise_noalloc", "pc_get_stats", "pc_get_trace", "pc_checkpoint_write", "pc_checkpoint_read", "pc_batch_create", "pc_batch_destroy",
            "pc_batch_attach", "pc_batch_detach", "pc_batch_contract", "pc_batch_counters", "pc_batch_set_timing",
            "pc_projected_bytes", "pc_server_create", "pc_server_submit", "pc_server_wait", "pc_server_get_stats",
-           "pc_server_clock", "pc_server_destroy", "pc_measure_alu_peaks"]
+           "pc_server_clock", "pc_server_destroy", "pc_measure_alu_peaks", "pc_autotune", "pc_load_tuning"]
 
 
 def _p(t):
@@ -160,6 +160,8 @@ def load(path: str = LIB_PATH):
         "pc_batch_set_timing": ([vp, i32], i32),
         "pc_projected_bytes": ([i32, i32, i64], i64),
         "pc_measure_alu_peaks": ([i32, _p(dbl), _p(dbl)], i32),
+        "pc_autotune": ([i32, i32, vp, vp, C.c_char_p, vp], i32),
+        "pc_load_tuning": ([C.c_char_p], i32),
         "pc_server_create": ([_p(PcServerConfig), _p(vp)], i32),
         "pc_server_submit": ([vp, _p(PcRequest), _p(i64)], i32),
         "pc_server_wait": ([vp, i64, dbl, _p(PcResult), vp, vp], i32),
@@ -196,6 +198,25 @@ def measure_alu_peaks(device: int = 0) -> tuple[float, float]:
     if st != PC_OK:
         raise PcError(st, "pc_measure_alu_peaks")
     return a.value, b.value
+
+
+def autotune(shapes, path: str | None = None, device: int = 0) -> np.ndarray:
+    """pc_autotune over (row length, matrices per launch) shapes; returns ms[n][3] for group
+    widths 1, 2, 4 and installs the fastest width per shape."""
+    lib = load()
+    lens = np.ascontiguousarray([s[0] for s in shapes], dtype=np.int32)
+    bats = np.ascontiguousarray([s[1] for s in shapes], dtype=np.int32)
+    ms = np.zeros((len(shapes), 3))
+    st = lib.pc_autotune(device, len(shapes), _ptr(lens), _ptr(bats), path.encode() if path else None, _ptr(ms))
+    if st != PC_OK:
+        raise PcError(st, "pc_autotune")
+    return ms
+
+
+def load_tuning(path: str) -> None:
+    st = load().pc_load_tuning(path.encode())
+    if st != PC_OK:
+        raise PcError(st, "pc_load_tuning")
 
 
 def plan_routing(n_qubits: int, pairs: np.ndarray, split_index: int) -> np.ndarray:

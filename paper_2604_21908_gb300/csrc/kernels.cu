@@ -1175,17 +1175,32 @@ cudaError_t launch_jacobi_g(const typename JacTraits<R>::Task* d_tasks, int ntas
   return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<R, G>, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
 }
 
+// Group width table of the FP64 row-pair sweeps, filled by the autotuner (pc_autotune /
+// pc_load_tuning): entry [len bucket][pairs bucket] = warps per pair (1, 2, 4), 0 = use the
+// heuristic below.  len bucket = ceil(log2(longest row)), pairs bucket = floor(log2(pairs per
+// round)), both clamped to the table.
+int g_jac_tuning[JAC_TUNE_LEN][JAC_TUNE_PAIRS] = {};
+
+int tuned_group_width(int max_len, int total_pairs) {
+  int bl = 0, bp = 0;
+  while ((1 << bl) < max_len && bl < JAC_TUNE_LEN - 1) ++bl;
+  while ((2 << bp) <= total_pairs && bp < JAC_TUNE_PAIRS - 1) ++bp;
+  return g_jac_tuning[bl][bp];
+}
+
 // Group width: at least enough threads to hold the longest row in registers; wider (up to
-// four warps per pair) when a round has fewer pairs than the grid has warps.
+// four warps per pair) when a round has fewer pairs than the grid has warps; a tuned width,
+// when the table has one for the launch's shape, overrides the FP64 choice.
 template <typename R>
 cudaError_t launch_jacobi_t(const typename JacTraits<R>::Task* d_tasks, int ntasks, JacobiStatus* d_status,
                             int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count, int max_len,
-                            int total_pairs, cudaStream_t stream) {
+                            int total_pairs, cudaStream_t stream, int force_g = 0) {
   if (ntasks <= 0) return cudaSuccess;
   if (ntasks > JAC_MAX_TASKS) return cudaErrorInvalidValue;
   const int warps = sm_count * (JAC_THREADS / 32);
   int g = max_len <= 32 * JAC_E ? 1 : (max_len <= 64 * JAC_E ? 2 : 4);
   while (g < 4 && total_pairs > 0 && (long long)total_pairs * 2 * g <= warps) g *= 2;
+  if (force_g == 1 || force_g == 2 || force_g == 4) g = force_g;
   if (g == 1) return launch_jacobi_g<R, 1>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
   if (g == 2) return launch_jacobi_g<R, 2>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
   return launch_jacobi_g<R, 4>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, stream);
@@ -1193,9 +1208,18 @@ cudaError_t launch_jacobi_t(const typename JacTraits<R>::Task* d_tasks, int ntas
 
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,
                           unsigned int* d_bar, int* d_err, int sm_count, int max_len, int total_pairs,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int force_g) {
+  if (force_g == 0) force_g = tuned_group_width(max_len, total_pairs);
   return launch_jacobi_t<double>(d_tasks, ntasks, d_status, max_sweeps, d_bar, d_err, sm_count, max_len,
-                                 total_pairs, stream);
+                                 total_pairs, stream, force_g);
+}
+
+void set_jacobi_tuning(int bl, int bp, int g) {
+  if (bl >= 0 && bl < JAC_TUNE_LEN && bp >= 0 && bp < JAC_TUNE_PAIRS) g_jac_tuning[bl][bp] = g;
+}
+
+int jacobi_tuning(int bl, int bp) {
+  return (bl >= 0 && bl < JAC_TUNE_LEN && bp >= 0 && bp < JAC_TUNE_PAIRS) ? g_jac_tuning[bl][bp] : 0;
 }
 
 cudaError_t launch_jacobi32(const JacobiTask32* d_tasks, int ntasks, JacobiStatus* d_status, int max_sweeps,

@@ -2720,6 +2720,124 @@ pc_status pc_kernel_timers(pc_circuit* c, int64_t* launches, double* ms, double*
   return PC_OK;
 }
 
+pc_status pc_autotune(int32_t device, int32_t n_shapes, const int32_t* lens, const int32_t* batches,
+                      const char* path, double* ms_out) {
+  if (n_shapes < 1 || !lens || !batches) return PC_ERR_INVALID_ARG;
+  for (int i = 0; i < n_shapes; ++i)
+    if (lens[i] < 4 || lens[i] > 4096 || batches[i] < 1 || batches[i] > 64) return PC_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return PC_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PC_ERR_CUDA;
+  std::FILE* f = path ? std::fopen(path, "w") : nullptr;
+  if (path && !f) return PC_ERR_INVALID_ARG;
+  if (f) std::fprintf(f, "# FP64 Jacobi group width: len_bucket pairs_bucket width ms(w=1) ms(w=2) ms(w=4)\n");
+  pc_status res = PC_OK;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    res = PC_ERR_CUDA;
+  for (int i = 0; i < n_shapes && res == PC_OK; ++i) {
+    const int L = lens[i], T = batches[i];
+    const size_t cells = (size_t)L * L;
+    // T random square matrices (SplitMix64 uniforms), a pristine copy and a working copy
+    std::vector<double2> h(cells * T);
+    for (size_t e = 0; e < h.size(); ++e) {
+      const double a = (double)(splitmix64(0xA070u + (uint64_t)L, 2 * e) >> 11) * (1.0 / 9007199254740992.0);
+      const double b = (double)(splitmix64(0xA070u + (uint64_t)L, 2 * e + 1) >> 11) * (1.0 / 9007199254740992.0);
+      h[e] = make_double2(a - 0.5, b - 0.5);
+    }
+    double2 *d0 = nullptr, *d1 = nullptr;
+    double* nrm = nullptr;
+    int32_t* stamp = nullptr;
+    pc::JacobiTask* dt = nullptr;
+    pc::JacobiStatus* ds = nullptr;
+    unsigned int* bar = nullptr;
+    int* err = nullptr;
+    std::vector<pc::JacobiTask> ht(T);
+    if (cudaMalloc(&d0, h.size() * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&d1, h.size() * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&nrm, (size_t)T * L * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&stamp, (size_t)T * L * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&dt, T * sizeof(pc::JacobiTask)) != cudaSuccess ||
+        cudaMalloc(&ds, T * sizeof(pc::JacobiStatus)) != cudaSuccess ||
+        cudaMalloc(&bar, 2 * sizeof(unsigned int)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      res = PC_ERR_OOM;
+    }
+    if (res == PC_OK &&
+        (cudaMemcpyAsync(d0, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+      res = PC_ERR_CUDA;
+    for (int t = 0; t < T && res == PC_OK; ++t) {
+      pc::JacobiTask& j = ht[t];
+      j = pc::JacobiTask{};
+      j.X = d1 + (size_t)t * cells; j.nrm2 = nrm + (size_t)t * L; j.stamp = stamp + (size_t)t * L;
+      j.m = L; j.n = L; j.mp = L + (L & 1);
+    }
+    if (res == PC_OK && cudaMemcpyAsync(dt, ht.data(), T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      res = PC_ERR_CUDA;
+    const int pairs = T * ((L + (L & 1)) / 2);
+    double best_ms = 1e300, ms_g[3] = {0, 0, 0};
+    int best_g = 0;
+    for (int gi = 0; gi < 3 && res == PC_OK; ++gi) {
+      const int g = 1 << gi;
+      double best_rep = 1e300;
+      for (int rep = 0; rep < 3 && res == PC_OK; ++rep) {    // the first run warms up
+        float ms = 0.0f;
+        if (cudaMemcpyAsync(d1, d0, h.size() * sizeof(double2), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            pc::launch_init_stamps(dt, T, L, st) != cudaSuccess ||
+            cudaMemsetAsync(ds, 0, T * sizeof(pc::JacobiStatus), st) != cudaSuccess ||
+            cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st) != cudaSuccess ||
+            cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
+            pc::launch_jacobi(dt, T, ds, 2, bar, err, sms, L, pairs, st, g) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          res = PC_ERR_CUDA;
+          break;
+        }
+        if (rep > 0) best_rep = std::min(best_rep, (double)ms);
+      }
+      ms_g[gi] = best_rep;
+      if (best_rep < best_ms) { best_ms = best_rep; best_g = g; }
+    }
+    int herr = 0;
+    if (res == PC_OK && (cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || herr))
+      res = herr ? PC_ERR_TIMEOUT : PC_ERR_CUDA;
+    if (res == PC_OK) {
+      int bl = 0, bp = 0;
+      while ((1 << bl) < L && bl < pc::JAC_TUNE_LEN - 1) ++bl;
+      while ((2 << bp) <= pairs && bp < pc::JAC_TUNE_PAIRS - 1) ++bp;
+      pc::set_jacobi_tuning(bl, bp, best_g);
+      if (f) std::fprintf(f, "%d %d %d %.4f %.4f %.4f\n", bl, bp, best_g, ms_g[0], ms_g[1], ms_g[2]);
+      if (ms_out) for (int k = 0; k < 3; ++k) ms_out[3 * i + k] = ms_g[k];
+    }
+    cudaFree(d0); cudaFree(d1); cudaFree(nrm); cudaFree(stamp); cudaFree(dt); cudaFree(ds); cudaFree(bar); cudaFree(err);
+  }
+  if (f) std::fclose(f);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  return res;
+}
+
+pc_status pc_load_tuning(const char* path) {
+  if (!path) return PC_ERR_INVALID_ARG;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return PC_ERR_INVALID_ARG;
+  char line[512];
+  int n = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    int bl = -1, bp = -1, g = 0;
+    if (std::sscanf(line, "%d %d %d", &bl, &bp, &g) == 3 && (g == 1 || g == 2 || g == 4)) {
+      pc::set_jacobi_tuning(bl, bp, g);
+      ++n;
+    }
+  }
+  std::fclose(f);
+  return n > 0 ? PC_OK : PC_ERR_INVALID_ARG;
+}
+
 pc_status pc_measure_alu_peaks(int32_t device, double* fp64_tflops, double* fp32_tflops) {
   if (!fp64_tflops || !fp32_tflops) return PC_ERR_INVALID_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return PC_ERR_CUDA;

@@ -132,9 +132,17 @@ cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int 
 // Cooperative persistent Jacobi over all tasks.  bar = 2 unsigned ints (zeroed by the
 // caller), err = 1 int (zeroed): set to 1 if a grid barrier wait exceeded its limit.
 // total_pairs = sum over tasks of mp/2 (pairs per round); it sets the group width.
+// force_g: warps per row pair (1, 2, 4) for this launch; 0 = the tuning table, else the
+// heuristic.
 cudaError_t launch_jacobi(const JacobiTask* d_tasks, int ntasks, JacobiStatus* d_status,
                           int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count,
-                          int max_len, int total_pairs, cudaStream_t stream);
+                          int max_len, int total_pairs, cudaStream_t stream, int force_g = 0);
+// The FP64 sweeps' group-width table (see launch_jacobi): buckets ceil(log2(longest row)) and
+// floor(log2(pairs per round)).
+constexpr int JAC_TUNE_LEN = 14;
+constexpr int JAC_TUNE_PAIRS = 16;
+void set_jacobi_tuning(int len_bucket, int pairs_bucket, int g);
+int jacobi_tuning(int len_bucket, int pairs_bucket);
 cudaError_t launch_truncate(const JacobiTask* d_tasks, int ntasks, double eps, int chi_max,
                             int32_t* d_idx, int idx_stride, double* d_lam, double* d_sraw,
                             int lam_stride, TruncOut* d_out, cudaStream_t stream);

@@ -97,3 +97,14 @@ def test_config_validation_and_no_gpu_fails_loudly():
         assert lib.pc_create(C.byref(cfg), C.byref(h)) == -7
         with pytest.raises(binding.PcError):
             binding.Server(max_resident=1, memory_budget=1 << 20)
+
+
+def test_tuning_table_loads_on_the_host(tmp_path):
+    """pc_load_tuning parses a table without a GPU; a file with no valid entry is an error."""
+    good = tmp_path / "t.txt"
+    good.write_text("# header\n10 9 4 1.0 2.0 0.5\n")
+    binding.load_tuning(str(good))
+    bad = tmp_path / "b.txt"
+    bad.write_text("# nothing\n10 9 3\n")
+    with pytest.raises(binding.PcError):
+        binding.load_tuning(str(bad))
