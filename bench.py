@@ -489,7 +489,7 @@ def run_ours(args):
         step_ms = t_max / args.steps
         t_roof_ms = alg_flops / args.steps / (fp64_peak * 1e12) * 1e3
         cpu = None
-        if world == 1:
+        if world == 1 and not args.no_cpu_baseline:
             u, dt = oracle_sample_threads(seed, 20.0, cpu_cores())
             u1, dt1 = oracle_sample_threads(seed, 20.0, 1)
             cpu = {"value": u / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -586,6 +586,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the batching and serving measurements")
     ap.add_argument("--pre-sweeps", type=int, default=0, help="FP32 preconditioning sweep cap (0: library default)")
     ap.add_argument("--no-m0", action="store_true", help="skip the batches of independent updates")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host cores")
     ap.add_argument("--profile-case", action="store_true", help="run one M0 configuration and exit")
     ap.add_argument("--chi", type=int, default=256)
     ap.add_argument("--batch", type=int, default=4)

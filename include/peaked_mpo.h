@@ -287,10 +287,14 @@ pc_status pc_measure_alu_peaks(int32_t device, double* fp64_tflops, double* fp32
  * width in the process-wide table the launches consult (keyed by ceil(log2 row length) and
  * floor(log2 row pairs per round)), and appends the table entries to the text file `path`
  * (NULL: no file).  ms_out (may be NULL): double[n_shapes][3], milliseconds per width.  The
- * widths change only the rounding order of the sweeps. */
+ * width changes the speed only: the sweeps sum every inner product in one fixed order that
+ * depends on the row length alone, so a factorisation is bit-identical at every width (and in
+ * every launch it shares with other factorisations). */
 pc_status pc_autotune(int32_t device, int32_t n_shapes, const int32_t* lens, const int32_t* batches,
                       const char* path, double* ms_out);
-/* Installs a table written by pc_autotune (lines "len_bucket pairs_bucket width ..."). */
+/* Installs a table written by pc_autotune (lines "len_bucket pairs_bucket width ...", '#'
+ * lines are comments); a width of 0 restores the built-in choice for that entry.  Returns
+ * PC_ERR_INVALID_ARG if the file cannot be read or holds no valid line. */
 pc_status pc_load_tuning(const char* path);
 pc_status pc_reset_kernel_timers(pc_circuit* c, int32_t enable);
 

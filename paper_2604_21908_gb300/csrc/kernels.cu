@@ -228,14 +228,20 @@ struct Rot {
   R c, sn, wx, wy, zx, zy;
 };
 
-// [u, v] <- [c u - s e v, s u + c e v] with e = e^{-i phi} (exactly unitary for c^2+s^2=1, |e|=1)
+// Products that the compiler must not fuse into a neighbouring addition (an explicit rounding).
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// [u, v] <- [c u - s e v, s u + c e v] with e = e^{-i phi} (exactly unitary for c^2+s^2=1, |e|=1).
+// Written with explicit fused multiply-adds and unfused products, so no multiply-add is left for
+// the compiler to contract: the rounding is the same in every code path that applies a rotation.
 template <typename R, typename C>
 __device__ __forceinline__ void rot_apply(const Rot<R>& q, C& u, C& v) {
   C na, nb;
-  na.x = q.c * u.x - (q.wx * v.x - q.wy * v.y);
-  na.y = q.c * u.y - (q.wx * v.y + q.wy * v.x);
-  nb.x = q.sn * u.x + (q.zx * v.x - q.zy * v.y);
-  nb.y = q.sn * u.y + (q.zx * v.y + q.zy * v.x);
+  na.x = fma(q.c, u.x, -fma(q.wx, v.x, -mul_rn(q.wy, v.y)));
+  na.y = fma(q.c, u.y, -fma(q.wx, v.y, mul_rn(q.wy, v.x)));
+  nb.x = fma(q.sn, u.x, fma(q.zx, v.x, -mul_rn(q.zy, v.y)));
+  nb.y = fma(q.sn, u.y, fma(q.zx, v.y, mul_rn(q.zy, v.x)));
   u = na;
   v = nb;
 }
@@ -247,27 +253,67 @@ __device__ __forceinline__ R warp_sum_t(R v) {
   return v;
 }
 
-// Sum of four values over the GT threads of a group, identical on every thread.
-template <typename R, int G>
-__device__ __forceinline__ void group_sum4(R& a, R& b, R& c, R& d, R (*red)[4], int grp, int gl) {
-  a = warp_sum_t(a); b = warp_sum_t(b); c = warp_sum_t(c); d = warp_sum_t(d);
-  if constexpr (G > 1) {
-    const int w = gl >> 5;
-    if ((gl & 31) == 0) { red[w][0] = a; red[w][1] = b; red[w][2] = c; red[w][3] = d; }
-    __syncwarp();   // bar.sync wants each warp converged
-    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
-    a = b = c = d = R(0);
-#pragma unroll
-    for (int k = 0; k < G; ++k) { a += red[k][0]; b += red[k][1]; c += red[k][2]; d += red[k][3]; }
+// Inner products of a row pair in a fixed order that does not depend on the group width G, so a
+// task's rotations (and so its singular values and vectors) are bit-identical in every launch it
+// can be part of (alone, batched, any tuned width).  The row, padded to n_pad = 128 ceil(n / 128),
+// is cut into four quarters of qseg = n_pad / 128 segments of 32 elements; lane l sums, per quarter,
+// its elements 32 s + l in increasing s as one FMA chain (jac_accum); the quarter sums are added as
+// (Q0 + Q1) + (Q2 + Q3) and then reduced over the 32 lanes by an xor butterfly (jac_reduce).  In a
+// group of G warps, warp w owns quarters w (4 / G) ... (w + 1)(4 / G) - 1.
+// a[0] += |u|^2, a[1] += |v|^2 (only when exact), a[2] + i a[3] += conj(u) v
+template <typename R, typename C>
+__device__ __forceinline__ void jac_accum(R (&a)[4], const C u, const C v, bool exact) {
+  a[2] = fma(u.x, v.x, fma(u.y, v.y, a[2]));
+  a[3] = fma(u.x, v.y, fma(-u.y, v.x, a[3]));
+  if (exact) {
+    a[0] = fma(u.x, u.x, fma(u.y, u.y, a[0]));
+    a[1] = fma(v.x, v.x, fma(v.y, v.y, a[1]));
   }
 }
+
+// The quarter sums of the group's threads -> the four totals, identical on every thread of the
+// group.  xs: this group's exchange slab in shared memory, [4][32 G] values (unused for G = 1).
+template <typename R, int G>
+__device__ __forceinline__ void jac_reduce(R (&acc)[4 / G][4], R* xs, int grp, int gl, R& a, R& b, R& c,
+                                           R& d) {
+  constexpr int GT = 32 * G;
+  R t[4];
+  if constexpr (G == 1) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) t[v] = (acc[0][v] + acc[1][v]) + (acc[2][v] + acc[3][v]);
+  } else {
+    const int lane = gl & 31;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if constexpr (G == 2) xs[v * GT + gl] = acc[0][v] + acc[1][v];
+      else xs[v * GT + gl] = acc[0][v];
+    }
+    __syncwarp();   // bar.sync wants each warp converged
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GT) : "memory");
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const R* x = xs + v * GT + lane;
+      if constexpr (G == 2) t[v] = x[0] + x[32];
+      else t[v] = (x[0] + x[32]) + (x[64] + x[96]);
+    }
+  }
+  a = warp_sum_t(t[0]);
+  b = warp_sum_t(t[1]);
+  c = warp_sum_t(t[2]);
+  d = warp_sum_t(t[3]);
+}
+
+// Bytes of dynamic shared memory of jacobi_kernel<R, G>: the double-buffered exchange slabs.
+template <typename R, int G>
+constexpr int jac_dyn_smem() { return G == 1 ? 0 : 2 * JAC_THREADS * 4 * (int)sizeof(R); }
 
 // One-sided (Hestenes) Jacobi on the rows of each task's matrix: rotate pairs of rows until
 // every pair is orthogonal to |<x_a, x_b>| <= tol |x_a| |x_b|, tol = 2 eps sqrt(n) (eps the
 // unit roundoff of R).  Pairs follow the round-robin (circle) ordering: in round r of a sweep
 // over mp rows, pair 0 = (mp-1, r), pair i = ((r+i) mod (mp-1), (r-i) mod (mp-1)).  Each
 // global iteration runs one round of every unfinished task (tasks of different sizes advance
-// their own sweeps), then all CTAs meet at a grid barrier.  A group of G warps rotates one pair.
+// their own sweeps), then all CTAs meet at a grid barrier.  A group of G warps rotates one pair;
+// its inner products follow the width-independent order of jac_accum / jac_reduce.
 // Squared row norms are computed exactly in round 0 of every sweep and carried through the
 // sweep with the exact-arithmetic update a' = a - t|g|, b' = b + t|g|; a sweep with no
 // rotation leaves them untouched, so the convergence decision always uses exact norms.
@@ -283,7 +329,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
   __shared__ int s_off[JAC_MAX_TASKS + 1];
   __shared__ unsigned char s_done[JAC_MAX_TASKS];
   __shared__ Task s_task[JAC_MAX_TASKS];
-  __shared__ R s_red[2][NG][G][4];
+  extern __shared__ __align__(16) unsigned char jac_dyn[];
+  R* const s_xch = reinterpret_cast<R*>(jac_dyn);     // [2][JAC_THREADS][4] when G > 1
   __shared__ R s_rot[NG][8];
   __shared__ R s_dead2[JAC_MAX_TASKS];
   __shared__ R s_marg2[JAC_MAX_TASKS];
@@ -353,23 +400,35 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         const int prev = (int)(g - Rr);
         if (tk.stamp[a] < prev && tk.stamp[b] < prev) continue;
       }
-      R (*red)[4] = s_red[parity][grp];
+      R* const xs = s_xch + (size_t)parity * JAC_THREADS * 4 + (size_t)grp * GT * 4;
+      const int n = tk.n;
+      const int qseg = (n + 127) >> 7;                    // 32-element segments per quarter
+      const int lane = gl & 31, wq = (gl >> 5) * (4 / G);  // this warp's first quarter
+      R acc[4 / G][4];
+#pragma unroll
+      for (int ql = 0; ql < 4 / G; ++ql) acc[ql][0] = acc[ql][1] = acc[ql][2] = acc[ql][3] = R(0);
       if (a >= tk.m || b >= tk.m) {
         // the padding row: in round 0 the real row still gets its exact norm
         if (full) {
           const int v = a < tk.m ? a : b;
-          const C* xv = tk.X + (size_t)v * tk.n;
-          R acc = R(0), z1 = R(0), z2 = R(0), z3 = R(0);
-          for (int k = gl; k < tk.n; k += GT) acc = fma(xv[k].x, xv[k].x, fma(xv[k].y, xv[k].y, acc));
-          group_sum4<R, G>(acc, z1, z2, z3, red, grp, gl);
-          if (gl == 0) tk.nrm2[v] = acc;
+          const C* xv = tk.X + (size_t)v * n;
+#pragma unroll
+          for (int ql = 0; ql < 4 / G; ++ql) {
+            const int k0 = 32 * (wq + ql) * qseg + lane;
+            for (int j = 0; j < qseg; ++j) {
+              const int k = k0 + 32 * j;
+              if (k < n) jac_accum(acc[ql], xv[k], xv[k], true);
+            }
+          }
+          R nv, z1, z2, z3;
+          jac_reduce<R, G>(acc, xs, grp, gl, nv, z1, z2, z3);
+          if (gl == 0) tk.nrm2[v] = nv;
           parity ^= 1;
         }
         continue;
       }
-      C* xa = tk.X + (size_t)a * tk.n;
-      C* xb = tk.X + (size_t)b * tk.n;
-      const int n = tk.n;
+      C* xa = tk.X + (size_t)a * n;
+      C* xb = tk.X + (size_t)b * n;
       // the carried norms, fetched early so their latency overlaps the row loads
       R na_pre = R(0), nb_pre = R(0);
       bool exact = full;
@@ -379,38 +438,32 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
         exact = !(fmin(na_pre, nb_pre) > JacTraits<R>::recompute * fmax(na_pre, nb_pre)) ||
                 fabs(na_pre - nb_pre) < JacTraits<R>::degenerate * (na_pre + nb_pre);
       }
-      const bool in_regs = n <= GT * JAC_E;
+      // register slot e holds segment (wq + e / (2G)) qseg + e % (2G) of the pair when the row fits
+      const bool in_regs = qseg <= 2 * G;
       C ra[JAC_E], rb[JAC_E];
-      R aa = R(0), bb = R(0), gr = R(0), gi = R(0);
       if (in_regs) {
 #pragma unroll
         for (int e = 0; e < JAC_E; ++e) {
-          const int k = gl + e * GT;
-          ra[e] = k < n ? xa[k] : mk2(R(0), R(0));
-          rb[e] = k < n ? xb[k] : mk2(R(0), R(0));
+          const int j = e % (2 * G);
+          const int k = 32 * ((wq + e / (2 * G)) * qseg + j) + lane;
+          const bool ok = j < qseg && k < n;
+          ra[e] = ok ? xa[k] : mk2(R(0), R(0));
+          rb[e] = ok ? xb[k] : mk2(R(0), R(0));
         }
 #pragma unroll
-        for (int e = 0; e < JAC_E; ++e) {
-          const C u = ra[e], v = rb[e];
-          gr = fma(u.x, v.x, fma(u.y, v.y, gr));
-          gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
-          if (exact) {
-            aa = fma(u.x, u.x, fma(u.y, u.y, aa));
-            bb = fma(v.x, v.x, fma(v.y, v.y, bb));
-          }
-        }
+        for (int e = 0; e < JAC_E; ++e) jac_accum(acc[e / (2 * G)], ra[e], rb[e], exact);
       } else {
-        for (int k = gl; k < n; k += GT) {
-          const C u = xa[k], v = xb[k];
-          gr = fma(u.x, v.x, fma(u.y, v.y, gr));
-          gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
-          if (exact) {
-            aa = fma(u.x, u.x, fma(u.y, u.y, aa));
-            bb = fma(v.x, v.x, fma(v.y, v.y, bb));
+#pragma unroll
+        for (int ql = 0; ql < 4 / G; ++ql) {
+          const int k0 = 32 * (wq + ql) * qseg + lane;
+          for (int j = 0; j < qseg; ++j) {
+            const int k = k0 + 32 * j;
+            if (k < n) jac_accum(acc[ql], xa[k], xb[k], exact);
           }
         }
       }
-      group_sum4<R, G>(aa, bb, gr, gi, red, grp, gl);
+      R aa, bb, gr, gi;
+      jac_reduce<R, G>(acc, xs, grp, gl, aa, bb, gr, gi);
       parity ^= 1;
       // The rotation's scalars cost the same pipe time on every warp that computes them
       // (whatever its active lanes), so only the group's first warp does; it shares them
@@ -422,7 +475,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
       int rotate;
       if (G == 1 || gl < 32) {
         if (!exact) { aa = na_pre; bb = nb_pre; }
-        const R g2 = fma(gr, gr, gi * gi);
+        const R g2 = fma(gr, gr, mul_rn(gi, gi));
         const R tol = R(2) * eps * sqrt(R(n));
         // rows at the underflow floor are zero for every purpose here
         // Floors: no pair of two rows below dead2, and no pair of a row below dead2 with a row
@@ -449,7 +502,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
           const R ex = gr * inv_g, ey = -gi * inv_g;        // e^{-i phi}
           q.wx = q.sn * ex; q.wy = q.sn * ey;               // s e^{-i phi}
           q.zx = q.c * ex; q.zy = q.c * ey;                 // c e^{-i phi}
-          tg = tt * gabs;
+          tg = mul_rn(tt, gabs);
         }
         if constexpr (G > 1) {
           if (gl == 0) {
@@ -477,19 +530,27 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(const typename J
       if (in_regs) {
 #pragma unroll
         for (int e = 0; e < JAC_E; ++e) {
-          const int k = gl + e * GT;
-          if (k < n) {
+          const int j = e % (2 * G);
+          const int k = 32 * ((wq + e / (2 * G)) * qseg + j) + lane;
+          if (j < qseg && k < n) {
             rot_apply(q, ra[e], rb[e]);
             xa[k] = ra[e];
             xb[k] = rb[e];
           }
         }
       } else {
-        for (int k = gl; k < n; k += GT) {
-          C u = xa[k], v = xb[k];
-          rot_apply(q, u, v);
-          xa[k] = u;
-          xb[k] = v;
+#pragma unroll
+        for (int ql = 0; ql < 4 / G; ++ql) {
+          const int k0 = 32 * (wq + ql) * qseg + lane;
+          for (int j = 0; j < qseg; ++j) {
+            const int k = k0 + 32 * j;
+            if (k < n) {
+              C u = xa[k], v = xb[k];
+              rot_apply(q, u, v);
+              xa[k] = u;
+              xb[k] = v;
+            }
+          }
         }
       }
       if (tk.Q) {
@@ -658,7 +719,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) bjac_kernel(const typename JacT
           bb = red[pr][0][1] + red[pr][1][1];
           gr = red[pr][0][2] + red[pr][1][2];
           gi = red[pr][0][3] + red[pr][1][3];
-          const R g2 = fma(gr, gr, gi * gi);
+          const R g2 = fma(gr, gr, mul_rn(gi, gi));
           const R lo2 = fmin(aa, bb), hi2 = fmax(aa, bb);
           const bool rotate = !(aa < Tr::tiny || bb < Tr::tiny) && !(hi2 < dead2) && !(lo2 < dead2 && hi2 < marg2) &&
                               g2 >= Tr::g2min && (g2 > (tol * tol) * aa * bb);
@@ -1162,9 +1223,14 @@ cudaError_t launch_init_accumulators(const JacobiTask* d_tasks, int ntasks, int 
 template <typename R, int G>
 cudaError_t launch_jacobi_g(const typename JacTraits<R>::Task* d_tasks, int ntasks, JacobiStatus* d_status,
                             int max_sweeps, unsigned int* d_bar, int* d_err, int sm_count, cudaStream_t stream) {
+  constexpr int dyn = jac_dyn_smem<R, G>();
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel<R, G>, JAC_THREADS, 0);
+    if (dyn > 0) {
+      cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_kernel<R, G>, JAC_THREADS, dyn);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm > 1) blocks_per_sm = 1;
     if (blocks_per_sm < 1) return cudaErrorLaunchOutOfResources;
@@ -1172,7 +1238,8 @@ cudaError_t launch_jacobi_g(const typename JacTraits<R>::Task* d_tasks, int ntas
   const int grid = sm_count * blocks_per_sm;
   void* args[] = {(void*)&d_tasks, (void*)&ntasks, (void*)&d_status, (void*)&max_sweeps, (void*)&d_bar,
                   (void*)&d_err};
-  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<R, G>, dim3(grid), dim3(JAC_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<R, G>, dim3(grid), dim3(JAC_THREADS), args, dyn,
+                                     stream);
 }
 
 // Group width table of the FP64 row-pair sweeps, filled by the autotuner (pc_autotune /

@@ -2829,7 +2829,7 @@ pc_status pc_load_tuning(const char* path) {
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#') continue;
     int bl = -1, bp = -1, g = 0;
-    if (std::sscanf(line, "%d %d %d", &bl, &bp, &g) == 3 && (g == 1 || g == 2 || g == 4)) {
+    if (std::sscanf(line, "%d %d %d", &bl, &bp, &g) == 3 && (g == 0 || g == 1 || g == 2 || g == 4)) {
       pc::set_jacobi_tuning(bl, bp, g);
       ++n;
     }
