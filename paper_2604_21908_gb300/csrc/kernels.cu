@@ -806,6 +806,23 @@ __global__ void precond_init_kernel(const JacobiTask* __restrict__ t64, const Ja
   }
 }
 
+// FP64 <-> FP32 copies of the rows of a task's matrix (m x n, same layout in both tasks).
+__global__ void narrow_rows_kernel(const JacobiTask* __restrict__ t64, const JacobiTask32* __restrict__ t32) {
+  const JacobiTask a = t64[blockIdx.y];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)a.m * a.n) return;
+  const double2 v = a.X[e];
+  t32[blockIdx.y].X[e] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void widen_rows_kernel(const JacobiTask32* __restrict__ t32, const JacobiTask* __restrict__ t64) {
+  const JacobiTask32 b = t32[blockIdx.y];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)b.m * b.n) return;
+  const float2 v = b.X[e];
+  t64[blockIdx.y].X[e] = make_double2((double)v.x, (double)v.y);
+}
+
 // Squared Frobenius norm of each task's FP64 matrix (fixed-order block reduction).
 __global__ void __launch_bounds__(1024) fro2_kernel(const JacobiTask* __restrict__ t64, double* out) {
   __shared__ double red[32];
@@ -1331,6 +1348,24 @@ cudaError_t launch_precond_init(const JacobiTask* d_t64, const JacobiTask32* d_t
   const long long cells = (long long)max_m * (max_n > max_m ? max_n : max_m);
   dim3 grid((unsigned)((cells + 255) / 256), ntasks);
   precond_init_kernel<<<grid, 256, 0, stream>>>(d_t64, d_t32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow_rows(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m, int max_n,
+                               cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_m * max_n;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  narrow_rows_kernel<<<grid, 256, 0, stream>>>(d_t64, d_t32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_rows(const JacobiTask32* d_t32, const JacobiTask* d_t64, int ntasks, int max_m, int max_n,
+                              cudaStream_t stream) {
+  if (ntasks <= 0) return cudaSuccess;
+  const long long cells = (long long)max_m * max_n;
+  dim3 grid((unsigned)((cells + 255) / 256), ntasks);
+  widen_rows_kernel<<<grid, 256, 0, stream>>>(d_t32, d_t64);
   return cudaGetLastError();
 }
 

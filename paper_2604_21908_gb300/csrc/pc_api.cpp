@@ -693,12 +693,13 @@ int trial_threshold(const FlatTask& f) {
 constexpr int kCertOversample = 32;
 constexpr int kCertMinVectors = 128;
 
-// Scratch of one certificate: X and T0 of the trial (m x n each) and C = P X^H (r x v) with
-// its Jacobi and truncation vectors.
+// Scratch of one certificate: X and T0 of the trial (m x n each), C = P X^H (r x v) with its
+// FP32 copy, and the Jacobi and truncation vectors.
 size_t cert_bytes(int m, int n, int r) {
   const size_t v = (size_t)std::min(m, n);
   return 2 * al256((size_t)m * n * sizeof(double2)) + al256((size_t)r * v * sizeof(double2)) +
-         3 * al256((size_t)r * sizeof(double)) + 2 * al256((size_t)r * sizeof(int32_t));
+         al256((size_t)r * v * sizeof(float2)) + 3 * al256((size_t)r * sizeof(double)) +
+         3 * al256((size_t)r * sizeof(int32_t)) + al256((size_t)r * sizeof(float));
 }
 
 int cert_rows(const FlatTask& f) {
@@ -713,21 +714,41 @@ int cert_rows(const FlatTask& f) {
 
 // The certificate of a batch of unswap trials (Sec. II.B.2 needs only each trial's count).
 // For a trial with stored matrix Xs (v vectors of length L; its singular values are those of
-// the bond matrix) and threshold k: C = P Xs^H with the fixed projection P (r = k + 32
-// orthonormal rows), then the FP64 one-sided Jacobi on the r rows of C.  Interlacing gives
-// sigma_k(X) >= sigma_k(C) / |P|_2, and |P|_2 <= |P|_F.  With the k-th largest converged row
-// norm c_k of C, the rounding of the product (|dC|_F <= 4 gamma_L |P|_F |X|_F), the backward
-// error of the sweeps (<= 16 S r u |C|_F) and the residual orthogonality of the converged rows
-// (cosines <= tol, so sigma_k >= c_k sqrt(1 - k tol)), the trial is certified to keep at least
-// k values when
-//     c_k sqrt(1 - k tol) - 4 gamma_L |P|_F |X|_F - 16 S r u |C|_F  >  eps |X|_F |P|_F,
+// the bond matrix) and threshold k: C = P Xs^H in FP64 with the fixed projection P (r = k + 32
+// orthonormal rows), then the one-sided Jacobi on the r rows of C, in FP32 (fp32: C rounded to
+// FP32 first) or in FP64.  Interlacing gives sigma_k(X) >= sigma_k(C) / |P|_2, and
+// |P|_2 <= |P|_F.  The converged rows are J (C + dC) with J unitary, where dC holds the FP64
+// product's rounding (|.|_F <= 4 gamma_L |P|_F |X|_F), the rounding to FP32 (<= u32 |C|_F, FP32
+// only) and the backward error of the sweeps (<= 16 S r u |C|_F, S sweeps, u the unit roundoff
+// of the sweeps; r counts the rotations of a row per sweep, ~2 r in the blocked FP32 kernel);
+// their mutual cosines are below cos = tol + 3 gamma_v (the convergence test's
+// tolerance plus the rounding of its inner products and norms), so by Gershgorin on the top k
+// rows sigma_k >= c_k sqrt(1 - (k - 1) cos), with c_k the k-th largest converged row norm.  The
+// trial is certified to keep at least k values when
+//     c_k sqrt(1 - (k - 1) cos) - 4 gamma_L |P|_F |X|_F - |dC from the sweeps| > eps |X|_F |P|_F,
 // since s_0 <= |X|_F.  Certified trials are rejected without factorising the bond matrix;
-// the others are resolved[] = 0 and run the full factorisation afterwards.
+// the others stay resolved[] = 0.  The FP32 pass is cheap (the FP32 pipe of this part is ~60
+// times its FP64 pipe) but its error term, ~6e-3 |C|_F at r = 288 and 12 sweeps, certifies only trials whose
+// k-th value is well above that; the FP64 pass certifies down to ~1e-11 |C|_F.
 pc_status certify_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, size_t b1,
-                        std::vector<char>& resolved) {
+                        std::vector<char>& resolved, bool fp32) {
   const int T = (int)(b1 - b0);
   cudaStream_t s = w->stream;
   size_t need = 0;
+  // position i of every launch array holds task ord[i]: rows of at most 1024 elements first
+  // (the blocked FP32 kernel), the longer ones after (the row-pair FP32 kernel)
+  std::vector<int> ord;
+  auto vec_len = [&](int t) {
+    const FlatTask& f = flat[b0 + t];
+    pc_circuit* c = f.r->c;
+    const int j = (*f.r->items)[f.k].bond;
+    return std::min(4 * c->chi[j], 4 * c->chi[j + 2]);
+  };
+  for (int t = 0; t < T; ++t)
+    if (vec_len(t) <= 1024) ord.push_back(t);
+  const int Tb = (int)ord.size();
+  for (int t = 0; t < T; ++t)
+    if (vec_len(t) > 1024) ord.push_back(t);
   for (int t = 0; t < T; ++t) {
     const FlatTask& f = flat[b0 + t];
     pc_circuit* c = f.r->c;
@@ -743,73 +764,102 @@ pc_status certify_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, si
   };
   std::vector<MergeIn> in(T);
   std::vector<int> kk(T), rr(T), vv(T), ll(T);
-  int max_r = 0, max_v = 0, pairs = 0;
-  for (int t = 0; t < T; ++t) {
-    const FlatTask& f = flat[b0 + t];
+  int max_r = 0, max_v = 0, max_vb = 1, max_ve = 1, pairs_e = 0, pairs_b = 0;
+  for (int i = 0; i < T; ++i) {
+    const FlatTask& f = flat[b0 + ord[i]];
     pc_circuit* c = f.r->c;
     const WaveItem& it = (*f.r->items)[f.k];
     const int j = it.bond;
     const int m = 4 * c->chi[j], n = 4 * c->chi[j + 2];
     const int v = std::min(m, n), L = std::max(m, n);
     const int r = cert_rows(f);
-    kk[t] = trial_threshold(f); rr[t] = r; vv[t] = v; ll[t] = L;
-    in[t] = {c, &it, (double2*)take((size_t)m * n * sizeof(double2)), (double2*)take((size_t)m * n * sizeof(double2))};
+    kk[i] = trial_threshold(f); rr[i] = r; vv[i] = v; ll[i] = L;
+    in[i] = {c, &it, (double2*)take((size_t)m * n * sizeof(double2)), (double2*)take((size_t)m * n * sizeof(double2))};
     double2* Cm = (double2*)take((size_t)r * v * sizeof(double2));
     double2* P = nullptr;
     WS_TRY(srft_matrix(w, L, r, &P));
-    pc::GemmDesc& g = w->h_cg[t];
+    pc::GemmDesc& g = w->h_cg[i];
     g = pc::GemmDesc{};
     g.A = P; g.lda = L;
-    g.B = in[t].X; g.ldb = L; g.opB = 1;     // the stored matrix: v rows of length L
+    g.B = in[i].X; g.ldb = L; g.opB = 1;     // the stored matrix: v rows of length L
     g.C = Cm; g.ldc = v;
     g.M = r; g.N = v; g.K = L; g.alpha = 1.0;
-    pc::JacobiTask& jc = w->h_jc[t];
+    pc::JacobiTask& jc = w->h_jc[i];
     jc = pc::JacobiTask{};
     jc.X = Cm;
     jc.Q = nullptr;
     jc.nrm2 = (double*)take((size_t)r * sizeof(double));
-    jc.fro2 = w->d_cfro2 + t;
+    jc.fro2 = w->d_cfro2 + i;
     jc.stamp = (int32_t*)take((size_t)r * sizeof(int32_t));
     jc.dead2_ovr = nullptr;
     const double dr = c->ctx->cfg.eps / (10.0 * r);
     jc.dead_rel = dr * dr;
     jc.m = r; jc.n = v; jc.mp = r + (r & 1);
-    pc::TruncTask& tt = w->h_tc[t];
+    pc::JacobiTask32& j32 = w->h_j32[i];
+    j32 = pc::JacobiTask32{};
+    j32.X = (float2*)take((size_t)r * v * sizeof(float2));
+    j32.Q = nullptr;
+    j32.nrm2 = (float*)take((size_t)r * sizeof(float));
+    j32.fro2 = jc.fro2;
+    j32.stamp = (int32_t*)take((size_t)r * sizeof(int32_t));
+    j32.dead2_ovr = nullptr;
+    j32.dead_rel = jc.dead_rel;
+    j32.m = jc.m; j32.n = jc.n; j32.mp = jc.mp;
+    pc::TruncTask& tt = w->h_tc[i];
     tt = pc::TruncTask{};
     tt.X = Cm;
     tt.idx = (int32_t*)take((size_t)r * sizeof(int32_t));
     tt.lam = (double*)take((size_t)r * sizeof(double));
     tt.sraw = (double*)take((size_t)r * sizeof(double));
-    tt.out = w->d_ctout + t;
+    tt.out = w->d_ctout + i;
     tt.eps = 0.0;
     tt.m = r; tt.n = v;
-    tt.chi_max = kk[t];
+    tt.chi_max = kk[i];
     // the bond matrix's own Jacobi task (for |X|_F^2)
-    pc::JacobiTask& jt = w->h_jt[t];
+    pc::JacobiTask& jt = w->h_jt[i];
     jt = pc::JacobiTask{};
-    jt.X = in[t].X; jt.m = v; jt.n = L; jt.mp = v + (v & 1);
+    jt.X = in[i].X; jt.m = v; jt.n = L; jt.mp = v + (v & 1);
     max_r = std::max(max_r, r); max_v = std::max(max_v, v);
-    pairs += jc.mp / 2;
+    if (i < Tb) { max_vb = std::max(max_vb, v); pairs_b += jc.mp / 2; }
+    else { max_ve = std::max(max_ve, v); pairs_e += jc.mp / 2; }
   }
   WS_TRY(stage_merge_gate(w, in));
   timer_mark(w, 1);
   WS_TRY(cudaMemcpyAsync(w->d_jt, w->h_jt, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
   WS_TRY(cudaMemcpyAsync(w->d_cg, w->h_cg, T * sizeof(pc::GemmDesc), cudaMemcpyHostToDevice, s));
   WS_TRY(cudaMemcpyAsync(w->d_jc, w->h_jc, T * sizeof(pc::JacobiTask), cudaMemcpyHostToDevice, s));
+  WS_TRY(cudaMemcpyAsync(w->d_j32, w->h_j32, T * sizeof(pc::JacobiTask32), cudaMemcpyHostToDevice, s));
   WS_TRY(cudaMemcpyAsync(w->d_tc, w->h_tc, T * sizeof(pc::TruncTask), cudaMemcpyHostToDevice, s));
   WS_TRY(pc::launch_fro2(w->d_jt, T, w->d_fro2, s));
   WS_TRY(pc::launch_gemm(w->d_cg, T, max_r, max_v, s));
   WS_TRY(pc::launch_fro2(w->d_jc, T, w->d_cfro2, s));
-  WS_TRY(pc::launch_init_stamps(w->d_jc, T, max_r, s));
   WS_TRY(cudaMemsetAsync(w->d_jst3, 0, T * sizeof(pc::JacobiStatus), s));
-  WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
   int max_sweeps = 1;
   for (int t = 0; t < T; ++t) max_sweeps = std::max(max_sweeps, flat[b0 + t].r->c->ctx->cfg.jacobi_max_sweeps);
-  WS_TRY(pc::launch_jacobi(w->d_jc, T, w->d_jst3, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_v, pairs, s));
+  if (fp32) {
+    WS_TRY(pc::launch_narrow_rows(w->d_jc, w->d_j32, T, max_r, max_v, s));
+    WS_TRY(pc::launch_init_stamps32(w->d_j32, T, max_r, s));
+    if (Tb > 0) {
+      WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+      WS_TRY(pc::launch_jacobi32_blocked(w->d_j32, Tb, w->d_jst3, max_sweeps, w->d_bar, w->d_err, w->sm_count,
+                                         max_vb, s));
+    }
+    if (T > Tb) {
+      WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+      WS_TRY(pc::launch_jacobi32(w->d_j32 + Tb, T - Tb, w->d_jst3 + Tb, max_sweeps, w->d_bar, w->d_err, w->sm_count,
+                                 max_ve, pairs_e, s));
+    }
+    WS_TRY(pc::launch_widen_rows(w->d_j32, w->d_jc, T, max_r, max_v, s));
+  } else {
+    WS_TRY(pc::launch_init_stamps(w->d_jc, T, max_r, s));
+    WS_TRY(cudaMemsetAsync(w->d_bar, 0, 2 * sizeof(unsigned int), s));
+    WS_TRY(pc::launch_jacobi(w->d_jc, T, w->d_jst3, max_sweeps, w->d_bar, w->d_err, w->sm_count, max_v,
+                             pairs_e + pairs_b, s));
+  }
   WS_TRY(pc::launch_truncate_tasks(w->d_tc, T, s));
   timer_mark(w, 2);
-  w->t_launch[5] += 3;
-  w->t_launch[4] += 3;
+  w->t_launch[5] += fp32 ? 3 + (Tb > 0) + (T > Tb) : 3;
+  w->t_launch[4] += fp32 ? 4 : 3;
   WS_TRY(cudaMemcpyAsync(w->h_ctout, w->d_ctout, T * sizeof(pc::TruncOut), cudaMemcpyDeviceToHost, s));
   WS_TRY(cudaMemcpyAsync(w->h_jst3, w->d_jst3, T * sizeof(pc::JacobiStatus), cudaMemcpyDeviceToHost, s));
   WS_TRY(cudaMemcpyAsync(w->h_fro2, w->d_fro2, T * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -823,28 +873,33 @@ pc_status certify_chunk(Workspace* w, std::vector<FlatTask>& flat, size_t b0, si
     w->t_ms[0] += a;
     w->t_ms[5] += b;
   }
-  for (int t = 0; t < T; ++t)   // the projection GEMM and the rotations of the FP64 sweeps
-    w->t_flops[5] += 8.0 * rr[t] * (double)vv[t] * ll[t] + 12.0 * w->h_jst3[t].sweeps * (double)rr[t] * rr[t] * vv[t];
+  for (int i = 0; i < T; ++i)   // the FP64 projection GEMM and the rotations of the sweeps
+    w->t_flops[5] += 8.0 * rr[i] * (double)vv[i] * ll[i] + 12.0 * w->h_jst3[i].sweeps * (double)rr[i] * rr[i] * vv[i];
   if (w->h_err[0]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "Jacobi grid barrier wait exceeded its limit");
   if (w->h_err[1]) return chunk_fail(flat, b0, b1, PC_ERR_TIMEOUT, "a tensor-core merge wait exceeded its limit");
-  const double u = 1.1102230246251565e-16;
-  for (int t = 0; t < T; ++t) {
-    const FlatTask& f = flat[b0 + t];
-    const pc::TruncOut& o = w->h_ctout[t];
-    const pc::JacobiStatus& js = w->h_jst3[t];
-    const int k = kk[t], r = rr[t], L = ll[t], v = vv[t];
-    const double xf = std::sqrt(std::max(0.0, w->h_fro2[t])), cf = std::sqrt(std::max(0.0, w->h_cfro2[t]));
+  const double u = 1.1102230246251565e-16;      // FP64 unit roundoff, 2^-53
+  const double us = fp32 ? 5.9604644775390625e-08 : u;   // unit roundoff of the sweeps (FP32: 2^-24)
+  for (int i = 0; i < T; ++i) {
+    const FlatTask& f = flat[b0 + ord[i]];
+    const pc::TruncOut& o = w->h_ctout[i];
+    const pc::JacobiStatus& js = w->h_jst3[i];
+    const int k = kk[i], r = rr[i], L = ll[i], v = vv[i];
+    const double xf = std::sqrt(std::max(0.0, w->h_fro2[i])), cf = std::sqrt(std::max(0.0, w->h_cfro2[i]));
     const double pf = std::sqrt((double)r) * (1.0 + 1e-12);
     const double gam = L * u / (1.0 - L * u);
-    const double tol = 2.0 * u * std::sqrt((double)v);
-    const double dead = std::sqrt(w->h_jc[t].dead_rel) * cf, marg = std::sqrt(6.0 * r) * dead;
+    const double gam_v = v * us / (1.0 - v * us);
+    const double cosb = 2.0 * (2.0 * us) * std::sqrt((double)v) + 3.0 * gam_v;   // tol = 2 eps sqrt(v), eps = 2 u
+    const double dead = std::sqrt(w->h_jc[i].dead_rel) * cf, marg = std::sqrt(6.0 * r) * dead;
     const double ck = o.s_last_kept;
-    const double lower = ck * std::sqrt(std::max(0.0, 1.0 - k * tol)) - 4.0 * gam * pf * xf -
-                         16.0 * js.sweeps * (double)r * u * cf;
+    // rotations a row takes part in per sweep: r - 1 in the row-pair kernel; in the blocked FP32
+    // kernel 15 per block round (the inner sweep over its 16-row block pair), ceil(r / 8) rounds
+    const double rot = (fp32 && i < Tb) ? 15.0 * ((r + 7) / 8 + 1) : (double)r;
+    const double lower = ck * std::sqrt(std::max(0.0, 1.0 - (k - 1) * cosb)) - 4.0 * gam * pf * xf -
+                         ((fp32 ? 1.0 : 0.0) + 16.0 * js.sweeps * rot) * us * cf;
     const double eps = f.r->c->ctx->cfg.eps;
     const bool ok = js.converged && o.count == k && ck > marg && lower > eps * xf * pf;
     if (ok) {
-      resolved[b0 + t] = 1;
+      resolved[b0 + ord[i]] = 1;
       f.r->counts[f.k] = k;
       f.r->accepted[f.k] = 0;
       f.r->c->stats.n_trials_certified += 1;
@@ -1245,20 +1300,30 @@ pc_status execute_waves(Workspace* w, std::vector<WaveReq*>& reqs) {
   for (const FlatTask& f : all)
     if (f.r->c->ctx->cfg.certify_trials && cert_rows(f) > 0) cand.push_back(f);
   std::vector<char> resolved(cand.size(), 0);
-  for (size_t pos = 0; pos < cand.size();) {
-    size_t end = pos, need = 0;
-    while (end < cand.size() && (int)(end - pos) < w->cap) {
-      const FlatTask& f = cand[end];
-      pc_circuit* c = f.r->c;
-      const int j = (*f.r->items)[f.k].bond;
-      const size_t b = cert_bytes(4 * c->chi[j], 4 * c->chi[j + 2], cert_rows(f));
-      if (need + b > w->arena_limit && end > pos) break;
-      need += b;
-      ++end;
+  // two passes: FP32 sweeps on every candidate, then FP64 sweeps on the ones the FP32 bound left
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<FlatTask> sub;
+    std::vector<size_t> at;
+    for (size_t i = 0; i < cand.size(); ++i)
+      if (!resolved[i]) { sub.push_back(cand[i]); at.push_back(i); }
+    std::vector<char> res(sub.size(), 0);
+    for (size_t pos = 0; pos < sub.size();) {
+      size_t end = pos, need = 0;
+      while (end < sub.size() && (int)(end - pos) < w->cap) {
+        const FlatTask& f = sub[end];
+        pc_circuit* c = f.r->c;
+        const int j = (*f.r->items)[f.k].bond;
+        const size_t b = cert_bytes(4 * c->chi[j], 4 * c->chi[j + 2], cert_rows(f));
+        if (need + b > w->arena_limit && end > pos) break;
+        need += b;
+        ++end;
+      }
+      pc_status st = certify_chunk(w, sub, pos, end, res, pass == 0);
+      if (st != PC_OK) worst = st;
+      pos = end;
     }
-    pc_status st = certify_chunk(w, cand, pos, end, resolved);
-    if (st != PC_OK) worst = st;
-    pos = end;
+    for (size_t i = 0; i < sub.size(); ++i)
+      if (res[i]) resolved[at[i]] = 1;
   }
   std::vector<FlatTask> flat;
   {

@@ -111,6 +111,11 @@ cudaError_t launch_gate_apply(const UpdateTask* d_tasks, int ntasks, int max_chi
 cudaError_t launch_precond_init(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m,
                                 int max_n, cudaStream_t stream);
 // Squared Frobenius norm of each task's FP64 matrix into d_out[t].
+// X32 = float(X) and X = double(X32) for each task pair (same m x n layout).
+cudaError_t launch_narrow_rows(const JacobiTask* d_t64, const JacobiTask32* d_t32, int ntasks, int max_m, int max_n,
+                               cudaStream_t stream);
+cudaError_t launch_widen_rows(const JacobiTask32* d_t32, const JacobiTask* d_t64, int ntasks, int max_m, int max_n,
+                              cudaStream_t stream);
 cudaError_t launch_fro2(const JacobiTask* d_t64, int ntasks, double* d_out, cudaStream_t stream);
 // Q64 = double(Q32) for every task (m x m).
 cudaError_t launch_widen_q(const JacobiTask32* d_t32, double2* const* d_q64, int ntasks, int max_m,
