@@ -108,3 +108,18 @@ def test_tuning_table_loads_on_the_host(tmp_path):
     bad.write_text("# nothing\n10 9 3\n")
     with pytest.raises(binding.PcError):
         binding.load_tuning(str(bad))
+
+
+def test_tuning_table_is_parsed_on_the_host(tmp_path):
+    """pc_load_tuning (host code, no GPU): '#' lines are comments, widths 1, 2, 4 are installed
+    and 0 restores the built-in choice; a file with no valid line or no file is rejected."""
+    good = tmp_path / "tuning.txt"
+    good.write_text("# len_bucket pairs_bucket width ms(w=1) ms(w=2) ms(w=4)\n"
+                    "10 2 4 1.0 2.0 3.0\n10 3 1 1.0 2.0 3.0\n10 2 0\n10 3 0\n")
+    binding.load_tuning(str(good))
+    bad = tmp_path / "bad.txt"
+    bad.write_text("# no entry\n10 2 3\n")
+    with pytest.raises(binding.PcError):
+        binding.load_tuning(str(bad))
+    with pytest.raises(binding.PcError):
+        binding.load_tuning(str(tmp_path / "missing.txt"))

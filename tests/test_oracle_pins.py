@@ -80,6 +80,30 @@ def test_perturbed_mirror_first_order_band():
     assert 0.8 < p.max() < 1.0
 
 
+@pytest.mark.parametrize("eps", [0.0, 0.02, 0.05])
+def test_perturbation_is_exp_i_eps_h_with_traceless_unit_norm_h(eps):
+    """The perturbation of the mirrored half (exp(i eps H), H random Hermitian; the paper does
+    not normalise H, the reading here is traceless with unit spectral norm): each gate of V^dagger
+    times its original gate of U is exp(i eps H_k), on the relabelled qubits in the same order.
+    Its eigenphases divided by eps are H_k's eigenvalues: they sum to 0 and the largest has
+    modulus 1.  A Frobenius normalisation, a trace left in, or another exponent convention
+    fails this; eps = 0 gives the identity."""
+    c = W.hidden_permutation_mirror(6, 10, eps, seed=3, store_complex64=False)
+    g, m = c.meta["gates_per_half"], c.meta["n_perm_gates"]
+    for k in range(g):
+        i = g + m + (g - 1 - k)                      # V^dagger holds U's gates in reverse order
+        assert tuple(c.pairs[i]) == (c.permutation[c.pairs[k][0]], c.permutation[c.pairs[k][1]])
+        e = c.mats[i] @ c.mats[k]
+        assert np.max(np.abs(e.conj().T @ e - np.eye(4))) < 1e-13
+        if eps == 0.0:
+            assert np.max(np.abs(e - np.eye(4))) < 1e-13
+            continue
+        lam = np.angle(np.linalg.eigvals(e)) / eps
+        assert abs(lam.sum()) < 1e-9
+        assert abs(np.max(np.abs(lam)) - 1.0) < 1e-9
+        assert np.max(np.abs(lam)) <= 1.0 + 1e-9
+
+
 # --- single-update math: closed forms --------------------------------------------------
 
 @pytest.mark.parametrize("name", ["SWAP", "CNOT", "product"])
