@@ -229,6 +229,27 @@ def test_mirror_invariant_brickwork12():
     assert abs(abs(psi[to_index(c.planted)]) ** 2 - 1.0) < 1e-12
 
 
+def test_trace_of_the_mirror_cancels_layer_pair_by_layer_pair():
+    """Fig. 3 telemetry on the unperturbed brickwork mirror, one layer pair per outer iteration
+    (tau = 1): absorbing the innermost layer of C_L (an adjoint layer of U) and of C_R (the same
+    layer of U) multiplies M by U_t^dagger ... U_t, so M returns to the identity after every
+    stage: each absorb record has every bond at dimension 1 (size(M) = 4n) and the two-qubit
+    gates absorbed grow by twice the brickwork layer size, counted here from the gate list
+    (layers of U alternate 6 and 5 gates on 12 qubits; the innermost is U's last)."""
+    n, layers = 12, 8
+    c = W.brickwork_mirror(n, layers, seed=4)
+    sizes = [len(range(t % 2, n - 1, 2)) for t in range(layers)]         # U's layers in time order
+    expect = list(2 * np.cumsum(sizes[::-1]))
+    r = mpo.contract(c, mpo.Config(eps=1e-12, chi_max=64, tau=1))
+    absorb = [rec for rec in r.trace if rec["phase"] == "absorb"]
+    assert len(absorb) >= layers
+    assert [rec["gates"] for rec in absorb[:layers]] == expect
+    for rec in absorb:
+        assert rec["size"] == 4 * n and rec["max_chi"] == 1
+    assert all(rec["accepted"] == 0 for rec in r.trace)
+    assert r.trace[-1]["gates"] == 2 * sum(sizes)
+
+
 @pytest.mark.parametrize("parallel", [True, False])
 def test_permutation_only_unswaps_to_product(parallel):
     """C = X^s P_pi as a SWAP network: unswapping extracts the whole permutation, every
