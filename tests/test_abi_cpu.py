@@ -46,6 +46,7 @@ def oracle_routing_plan(circuit):
     lambda: W.random_circuit(9, 60, seed=2),
     lambda: W.random_circuit(7, 30, seed=5, line=True),
     lambda: W.workload_unswap28(0),
+    lambda: W.hqap_like_mirror(56, 918, 27, 0.1, seed=0),     # the paper's shape: 1,917 two-qubit gates
 ])
 def test_router_plan_matches_oracle(maker):
     c = maker()
@@ -97,17 +98,6 @@ def test_config_validation_and_no_gpu_fails_loudly():
         assert lib.pc_create(C.byref(cfg), C.byref(h)) == -7
         with pytest.raises(binding.PcError):
             binding.Server(max_resident=1, memory_budget=1 << 20)
-
-
-def test_tuning_table_loads_on_the_host(tmp_path):
-    """pc_load_tuning parses a table without a GPU; a file with no valid entry is an error."""
-    good = tmp_path / "t.txt"
-    good.write_text("# header\n10 9 4 1.0 2.0 0.5\n")
-    binding.load_tuning(str(good))
-    bad = tmp_path / "b.txt"
-    bad.write_text("# nothing\n10 9 3\n")
-    with pytest.raises(binding.PcError):
-        binding.load_tuning(str(bad))
 
 
 def test_tuning_table_is_parsed_on_the_host(tmp_path):
