@@ -90,7 +90,9 @@ typedef struct pc_config {
                              /* factorisation when a rigorous lower bound shows that its   */
                              /* count reaches the rejection threshold (the k-th singular   */
                              /* value of a randomised FP64 projection, Sec. II.B.2 needs   */
-                             /* only the count); 0: every trial is a full factorisation.   */
+                             /* only the count), the projection's Jacobi run in FP32 and,  */
+                             /* for trials that bound leaves open, in FP64; decisions are  */
+                             /* those of full factorisations; 0: every trial is factorised */
   int32_t deflate;           /* 1: when the chi_max cap decides the count, the FP64 sweeps */
                              /* orthogonalise only what the kept vectors need (a floor set */
                              /* from the FP32 sweeps, verified afterwards); 0: off         */
@@ -264,7 +266,7 @@ pc_status pc_get_unswap_log(pc_circuit* c, int64_t cap, int32_t* rec, int64_t* n
 /* Kernel accounting since the last pc_reset_kernel_timers.  Per kernel class (0 merge and
  * gate, 1 Jacobi factorisation, 2 truncation, 3 split, 4 everything else: environments,
  * peak search, sampling, one-qubit gates, accumulator set-up, 5 unswap-trial certificates:
- * projection, FP64 sweeps and norms) the number of kernel launches and, when timing is
+ * projection, FP32 and FP64 sweeps and norms) the number of kernel launches and, when timing is
  * enabled, the total milliseconds measured with CUDA events on the circuit's stream (class 4
  * is counted, not timed) and the floating-point work:
  * class 0: 8 * 4chi_l * chi_m * 4chi_r + 8 * 256 * chi_l * chi_r (complex merge + gate);
