@@ -365,8 +365,10 @@ class Contraction:
 
         Pinned: trial counts equal brute-force operator-Schmidt ranks, strict acceptance lowers
         the total bond dimension, permutation-only circuits end at dimension 1 with the
-        permutation in the layouts, the operator is unchanged.  The accepted sequence on
-        perturbed circuits: parity unpinned (no closed form; compared with the GPU only)."""
+        permutation in the layouts, the operator is unchanged, and the log, layouts and final
+        operator equal a replay of this rule on the dense operator (N <= 6).  The accepted
+        sequence on perturbed circuits beyond that size: parity unpinned (no closed form;
+        compared with the GPU only)."""
         st = self.state
         accepted_total = 0
         for it in range(self.cfg.max_unswap_iter):

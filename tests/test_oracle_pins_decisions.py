@@ -1,6 +1,6 @@
 """Pins for the oracle's discrete decisions, against computations that share nothing with
-it: the sequential unswap selection rule replayed on the dense 4^n operator built from the
-statevector simulator, the stall flag on circuits whose size(M) is fixed by construction,
+it: the sequential (Algorithm 1) and parallel (App. A.1) unswap rules replayed on the dense 4^n
+operator built from the statevector simulator, the stall flag on circuits whose size(M) is fixed by construction,
 and the counter-based SplitMix64 stream against its published outputs.  CPU only."""
 import math
 
@@ -138,6 +138,74 @@ def test_sequential_replay_covers_every_side_and_a_rejection():
     assert steps > len(log)                       # some steps were rejections
     bonds = [b for (_, _, b) in log]
     assert len(bonds) > len(set(bonds))           # a bond was accepted again after re-enabling
+
+
+# --- parallel unswapping (App. A.1) replayed on the dense operator -----------------------
+
+_APP_A1_ORDER = [(mpo.SIDE_BOTH, 0), (mpo.SIDE_BOTH, 1), (mpo.SIDE_LEFT, 0), (mpo.SIDE_LEFT, 1),
+                 (mpo.SIDE_RIGHT, 0), (mpo.SIDE_RIGHT, 1)]
+
+
+def _replay_parallel(t, n, eps, chi_max, equal, max_iter, pos_l, pos_r):
+    """App. A.1 on the dense site tensor: cycles of six batches (both sides, then left, then
+    right; even bonds before odd ones); in a batch every bond of that parity is tried on the
+    pre-batch tensor and the swaps whose operator-Schmidt rank drops below the current one (or
+    does not grow, in equal mode) are applied (bonds of one parity share no site, so those swaps
+    commute and leave each other's cuts alone); a cycle with no acceptance, or max_iter cycles,
+    ends the stage."""
+    pos = {mpo.SIDE_LEFT: list(pos_l), mpo.SIDE_RIGHT: list(pos_r)}
+    log = []
+    for it in range(max_iter):
+        any_acc = False
+        for side, parity in _APP_A1_ORDER:
+            bonds = list(range(parity, n - 1, 2))
+            old = {b: _count(sv.operator_schmidt_values(t, b), eps, chi_max) for b in bonds}
+            new = {b: _count(sv.operator_schmidt_values(_swap_legs(t, n, b, side), b), eps, chi_max)
+                   for b in bonds}
+            for b in bonds:
+                if new[b] <= old[b] if equal else new[b] < old[b]:
+                    t = _swap_legs(t, n, b, side)
+                    log.append((it, side, b))
+                    any_acc = True
+                    for s_ in (mpo.SIDE_LEFT, mpo.SIDE_RIGHT):
+                        if side in (s_, mpo.SIDE_BOTH):
+                            p = pos[s_]
+                            x, y = p.index(b), p.index(b + 1)
+                            p[x], p[y] = b + 1, b
+        if not any_acc:
+            break
+    return log, t, pos
+
+
+@pytest.mark.parametrize("circ,equal,min_accepts", [
+    (W.hidden_permutation_mirror(6, 6, 0.0, seed=2), False, 3),
+    (W.permutation_only(6, seed=4), False, 2),
+    (W.permutation_only(6, seed=1), False, 2),
+    (W.random_circuit(6, 10, seed=3), False, 0),     # no swap lowers a rank: one empty cycle
+    (W.permutation_only(5, seed=2), True, 2),
+])
+def test_parallel_unswap_matches_brute_force(circ, equal, min_accepts):
+    """The oracle's parallel unswap log (cycle, side, bond), its layouts and its final operator
+    equal a replay of App. A.1 on the dense operator of the circuit (N <= 6)."""
+    n = circ.n_qubits
+    cfg = mpo.Config(eps=1e-9, chi_max=1 << 20, tau=1e12, unswap_enabled=False, unswap_parallel=True,
+                     accept_equal=equal, max_unswap_iter=3 if equal else 20)
+    ctr = mpo.Contraction(circ, cfg)
+    ctr.run()
+    pos_l, pos_r = list(ctr.lay[mpo.SIDE_LEFT].pos), list(ctr.lay[mpo.SIDE_RIGHT].pos)
+    t0 = sv.operator_to_sites(sv.full_operator(circ), n, pos_l, pos_r) / 2 ** (n / 2)
+    want_log, t_end, pos = _replay_parallel(t0, n, cfg.eps, cfg.chi_max, equal, cfg.max_unswap_iter,
+                                            pos_l, pos_r)
+    ctr.unswap_parallel()
+    got = [(it, side, bond) for (_, it, side, bond) in ctr.res.unswap_log]
+    assert got == want_log
+    assert ctr.lay[mpo.SIDE_LEFT].pos == pos[mpo.SIDE_LEFT]
+    assert ctr.lay[mpo.SIDE_RIGHT].pos == pos[mpo.SIDE_RIGHT]
+    t = ctr.state.B[0]
+    for j in range(1, n):
+        t = np.tensordot(t, ctr.state.B[j], axes=([-1], [0]))
+    assert np.max(np.abs(t.reshape([4] * n) - t_end)) < 1e-12
+    assert len(want_log) >= min_accepts
 
 
 # --- the stall flag (Sec. III.A progress rule) -------------------------------------------
